@@ -1,0 +1,126 @@
+"""Pins for the readings of the paper's rules (sequential restatements in
+oracle/method_ref.py) against the oracle's definition.
+
+Every sampling x linking x find (x splice) combination, Shiloach-Vishkin and
+the 16 Liu-Tarjan variants must reach the component labels of the definition,
+and every recorded spanning forest must pass the checker.  Planted wrong
+readings show the checks have teeth.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from oracle import method_ref as mr
+
+
+def _graphs():
+    out = []
+    for seed in range(3):
+        n = 60
+        out.append((n, graphgen.er(n, 45 + 20 * seed, 100 + seed)))
+    out.append((128, graphgen.rmat(7, 300, 7)))
+    n, e = graphgen.grid_paths(6, 0.2, 3, 12, 8)
+    out.append((n, e))
+    out.append((10, np.zeros((0, 2), np.uint32)))
+    return out
+
+
+GRAPHS = _graphs()
+
+COMBOS = []
+for link in ["async", "hooks", "early"]:
+    for f in ["naive", "compress", "split", "halve"]:
+        COMBOS.append((link, f, "splice"))
+for f in ["naive", "split", "halve"]:
+    for sp in ["split_one", "halve_one", "splice"]:
+        COMBOS.append(("remcas", f, sp))
+COMBOS += [("jtb", "naive", "splice"), ("jtb", "twotrysplit", "splice")]
+
+
+@pytest.mark.parametrize("sample", ["none", "kout", "hb", "bfs"])
+@pytest.mark.parametrize("link,find,splice", COMBOS)
+def test_static_conn_reading(sample, link, find, splice):
+    for n, e in GRAPHS:
+        ref = oracle.cc_uf(n, e)
+        off, cols = graphgen.csr(n, e)
+        lab, sf = mr.static_conn_csr(off.tolist(), cols.tolist(), sample, link, find, splice)
+        assert (np.array(lab, np.uint32) == ref).all()
+        assert oracle.sf_check_arcs(n, off, cols, np.array(sf, np.uint64), ref) == 0
+
+
+def test_coo_edge_order_irrelevant():
+    n, e = GRAPHS[0]
+    ref = oracle.cc_uf(n, e)
+    rng = np.random.default_rng(3)
+    for link, f, sp in COMBOS:
+        uf = mr.UF(n, link, f, sp)
+        sf = mr.finish_coo(e.tolist(), uf, order=rng.permutation(len(e)).tolist())
+        assert (np.array(uf.labels(), np.uint32) == ref).all()
+        assert oracle.sf_check(n, e, np.array(sf, np.uint64), ref) == 0
+
+
+def test_shiloach_vishkin_reading():
+    for n, e in GRAPHS:
+        lab, rounds = mr.shiloach_vishkin(n, [tuple(x) for x in e.tolist()])
+        assert (np.array(lab, np.uint32) == oracle.cc_uf(n, e)).all()
+
+
+@pytest.mark.parametrize("variant", mr.LT_VARIANTS)
+def test_liu_tarjan_reading(variant):
+    for n, e in GRAPHS:
+        lab, rounds = mr.liu_tarjan(n, [tuple(x) for x in e.tolist()], variant)
+        assert (np.array(lab, np.uint32) == oracle.cc_uf(n, e)).all()
+
+
+def test_most_frequent_label_tie_rule():
+    assert mr.most_frequent_label([3, 3, 1, 1, 2]) == 1
+    assert mr.most_frequent_label([5, 4, 4, 5, 5]) == 5
+
+
+def test_wrong_skip_rule_is_caught():
+    """Skipping edges of L_max vertices is only sound when every edge is seen
+    from both endpoints (symmetric CSR).  Over a one-direction COO list the
+    same rule drops edges: the definition catches it."""
+    n = 6
+    # sampled state: {0,1,2} merged (label 0 = L_max); edge (0, 5) listed once
+    edges = [(0, 1), (1, 2), (0, 5), (3, 4)]
+    uf = mr.UF(n)
+    for u, v in edges[:2]:
+        uf.union(u, v)
+    mr.full_shortcut(uf.P)
+    lmax = mr.most_frequent_label(uf.P)
+    lab0 = list(uf.P)
+    for u, v in edges:
+        if lab0[u] == lmax:          # vertex-skip rule applied to one-direction COO
+            continue
+        uf.union(u, v)
+    wrong = np.array(uf.labels(), np.uint32)
+    ref = oracle.cc_uf(n, np.array(edges, np.uint32))
+    assert not (wrong == ref).all()
+    # the COO reading (skip an edge only when both endpoints are L_max) is right
+    uf = mr.UF(n)
+    for u, v in edges[:2]:
+        uf.union(u, v)
+    mr.full_shortcut(uf.P)
+    lab0 = list(uf.P)
+    for u, v in edges:
+        if lab0[u] == lmax and lab0[v] == lmax:
+            continue
+        uf.union(u, v)
+    assert (np.array(uf.labels(), np.uint32) == ref).all()
+
+
+def test_parent_connect_to_endpoints_stalls():
+    """Reading check for ParentConnect: if the parents of an edge's endpoints
+    were sent to the endpoints themselves, root-only updates could never move a
+    non-root endpoint, and PRS would stop with two components unmerged."""
+    n = 4
+    edges = [(0, 2), (1, 3), (2, 3)]
+    P = [0, 1, 0, 1]                      # 2 -> 0 and 3 -> 1 already
+    # wrong reading: 2 receives P[3] = 1, 3 receives P[2] = 0, both non-roots
+    msg = {2: 1, 3: 0}
+    newP = [min(P[x], msg.get(x, P[x])) if P[x] == x else P[x] for x in range(n)]
+    assert newP == P                       # no progress: would end unmerged
+    lab, _ = mr.liu_tarjan(n, edges, "PRS", labels=P)
+    assert lab == [0, 0, 0, 0]
