@@ -1,0 +1,211 @@
+/*
+ * gconn.h -- C ABI of libgconn: static and incremental connected components
+ * and spanning forests on one GPU (sm_103a), by concurrent union-find.
+ *
+ * The method is the two-phase framework of Hong, Dhulipala and Shun,
+ * "Exploring the Design Space of Static and Incremental Graph Connectivity
+ * Algorithms on GPUs" (PACT 2020): initialise labels, sample a subgraph,
+ * find the most frequent label L_max, run a finish algorithm over the edges
+ * of vertices whose label is not L_max, then finalise the labels
+ * (Section 3.2, Algorithm 1); spanning forest (Algorithm 2); incremental
+ * batches of inserts and queries (Section 3.5, Algorithm 3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Vertex ids are uint32 in [0, n); n <= 0xFFFFFFFE (0xFFFFFFFF is reserved
+ *   as "none").  Edge lists (COO) are interleaved uint32 pairs
+ *   edges[2*i], edges[2*i+1].  CSR is offsets (uint64, n+1 entries,
+ *   offsets[n] = number of arcs) plus cols (uint32); it must be symmetric
+ *   (each undirected edge stored as both arcs) with every row sorted
+ *   ascending, as in Section 2 ("Graph Notation and Formats").
+ * - Self-loops and duplicate edges are accepted and change nothing.
+ * - Every pointer may be device memory or host memory (pageable or pinned);
+ *   the library checks each one.  Host inputs are copied to the device; host
+ *   outputs are filled before the call returns.  The caller owns every buffer
+ *   it passes; the library never frees caller memory.  Temporary device
+ *   memory comes from the device's stream-ordered pool (cudaMallocAsync) and
+ *   is returned on the same stream.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  With device-resident inputs and outputs every call only
+ *   enqueues work and returns; errors found on the device (an endpoint >= n,
+ *   an iteration cap reached) are reported by the next gconn_sync() on that
+ *   device.  With any host output the call synchronises the stream and
+ *   returns the device status itself.  Device error flags are per device and
+ *   shared by all calls on it.
+ * - Results are the canonical labelling: labels[v] = the smallest vertex id
+ *   of v's component, whatever variant computed them.
+ */
+#ifndef GCONN_H
+#define GCONN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+typedef enum gconn_status {
+    GCONN_OK = 0,
+    GCONN_E_INVAL = 1,          /* null pointer, bad size or malformed argument */
+    GCONN_E_RANGE = 2,          /* an endpoint or query vertex is >= n */
+    GCONN_E_NOMEM = 3,          /* device allocation failed */
+    GCONN_E_UNSUPPORTED = 4,    /* invalid variant combination for this input */
+    GCONN_E_NONCONVERGED = 5,   /* a device loop reached its iteration cap */
+    GCONN_E_CUDA = 6            /* a CUDA runtime call failed */
+} gconn_status;
+
+/* --------------------------------------------------------------- variants */
+/* Sampling phase (Section 3.3; Algorithms 2-4 of the appendix).  Sampling
+ * needs CSR input: the skip rule drops whole adjacency lists. */
+enum { GCONN_SAMPLE_NONE = 0, GCONN_SAMPLE_KOUT = 1, GCONN_SAMPLE_HB = 2, GCONN_SAMPLE_BFS = 3 };
+
+/* Finish algorithm (Section 3.4): union-find rules (Algorithms 7-9, 11 and
+ * Union-JTB), root-based Shiloach-Vishkin (Algorithm 12), Liu-Tarjan. */
+enum {
+    GCONN_LINK_ASYNC = 0, GCONN_LINK_HOOKS = 1, GCONN_LINK_EARLY = 2,
+    GCONN_LINK_REMCAS = 3, GCONN_LINK_JTB = 4, GCONN_LINK_SV = 5, GCONN_LINK_LT = 6
+};
+
+/* On-the-fly compression (Algorithm 5).  FULLSHORTCUT = no on-the-fly
+ * compression; the separate pointer-jumping pass (run after sampling and at
+ * finalisation for every variant) does all of it.  TWOTRYSPLIT is Union-JTB
+ * only; COMPRESS is not valid with Union-Rem-CAS (Section 3.4). */
+enum {
+    GCONN_FIND_NAIVE = 0, GCONN_FIND_COMPRESS = 1, GCONN_FIND_SPLIT = 2,
+    GCONN_FIND_HALVE = 3, GCONN_FIND_TWOTRYSPLIT = 4, GCONN_FIND_FULLSHORTCUT = 5
+};
+
+/* Splice step of Union-Rem-CAS (Algorithm 6); NONE selects SPLICE for Rem. */
+enum { GCONN_SPLICE_NONE = 0, GCONN_SPLICE_SPLIT_ONE = 1, GCONN_SPLICE_HALVE_ONE = 2, GCONN_SPLICE_SPLICE = 3 };
+
+/* Liu-Tarjan rule set (appendix list of 16 variants): connect rule in the
+ * low two bits, then flags.  E.g. PRS = GCONN_LT_PARENT | GCONN_LT_ROOTUPDATE. */
+enum {
+    GCONN_LT_CONNECT = 0, GCONN_LT_PARENT = 1, GCONN_LT_EXTENDED = 2,
+    GCONN_LT_ROOTUPDATE = 4, GCONN_LT_FULLSHORTCUT = 8, GCONN_LT_ALTER = 16
+};
+
+typedef struct gconn_variant {
+    int32_t sample;     /* GCONN_SAMPLE_* */
+    int32_t k;          /* k-out: edges per vertex (first k; default 2) */
+    int32_t hb_n;       /* HB: edges per remaining root (default 4) */
+    int32_t link;       /* GCONN_LINK_* */
+    int32_t find;       /* GCONN_FIND_* */
+    int32_t splice;     /* GCONN_SPLICE_* (Union-Rem-CAS only) */
+    int32_t lt_rules;   /* GCONN_LT_* bits (Liu-Tarjan only) */
+    int32_t block;      /* threads per block, 0 = library default */
+    uint64_t seed;      /* L_max / BFS-source sampling and Union-JTB priorities */
+    uint32_t iter_cap;  /* per-operation loop cap, 0 = default (2^24) */
+    uint32_t reserved;  /* must be 0 */
+} gconn_variant;
+
+/* Fill *v with the library default (Union-Async, naive find, k-out k=2 for
+ * CSR input and no sampling for COO input).  Returns GCONN_E_INVAL on NULL. */
+gconn_status gconn_variant_default(gconn_variant* v);
+
+/* Validate a variant for an input kind (0 = COO, 1 = CSR) and purpose
+ * (want_forest = 1 for a spanning forest or an incremental handle).  Returns
+ * GCONN_OK, GCONN_E_INVAL (value out of range) or GCONN_E_UNSUPPORTED (e.g.
+ * sampling on COO, COMPRESS with Rem-CAS, splice without Rem-CAS, TWOTRYSPLIT
+ * without JTB, a forest with a non-root-based Liu-Tarjan rule set). */
+gconn_status gconn_variant_check(const gconn_variant* v, int input_kind, int want_forest);
+
+/* -------------------------------------------------------- static: COO */
+/* Connected components of the graph with n vertices and m undirected edges
+ * (Algorithm 1 without a sampling phase; COO input, Section 2).
+ *   edges  : uint32[2m] interleaved pairs (device or host)
+ *   labels : uint32[n] output, canonical min-id labels (device or host)
+ *   v      : variant or NULL for the default; sampling must be NONE.
+ * labels doubles as the union-find parent array while the call runs.
+ * Errors: E_INVAL (null pointer with n or m > 0, n = 0xFFFFFFFF, reserved != 0),
+ * E_UNSUPPORTED (see gconn_variant_check), E_RANGE (endpoint >= n),
+ * E_NONCONVERGED, E_NOMEM, E_CUDA. */
+gconn_status gconn_cc(uint32_t n, uint64_t m, const uint32_t* edges, uint32_t* labels,
+                      const gconn_variant* v, void* stream);
+
+/* -------------------------------------------------------- static: CSR */
+/* Connected components from symmetric sorted CSR with the full two-phase
+ * method (Algorithm 1): sampling (k-out, HB or BFS), L_max, finish over the
+ * adjacency of vertices whose sampled label is not L_max, finalisation.
+ *   offsets : uint64[n+1], cols : uint32[offsets[n]]
+ *   labels  : uint32[n] output, canonical min-id labels.
+ * Errors as gconn_cc. */
+gconn_status gconn_cc_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
+                          uint32_t* labels, const gconn_variant* v, void* stream);
+
+/* ------------------------------------------------------ spanning forest */
+/* Spanning forest (Algorithm 2): every root that stops being a root records
+ * the input edge that linked it (Section 3.2).  Output ids are COO edge
+ * indices in [0, m), written unsorted to forest[0 .. count-1] (capacity n);
+ * count = n - (number of components).  m must be < 2^32 - 1.
+ *   forest       : uint64[n] output (device or host)
+ *   forest_count : uint64[1] output (device or host)
+ *   labels       : optional uint32[n] canonical labels (NULL = not wanted)
+ * Variant: no sampling; Liu-Tarjan only with RootUpdate rule sets. */
+gconn_status gconn_spanning_forest(uint32_t n, uint64_t m, const uint32_t* edges,
+                                   uint64_t* forest, uint64_t* forest_count, uint32_t* labels,
+                                   const gconn_variant* v, void* stream);
+
+/* Spanning forest from symmetric sorted CSR with sampling.  Output ids are
+ * arc positions a in [0, offsets[n]); arc a joins the row containing a to
+ * cols[a].  offsets[n] must be < 2^32 - 1.  Otherwise as above. */
+gconn_status gconn_spanning_forest_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
+                                       uint64_t* forest, uint64_t* forest_count, uint32_t* labels,
+                                       const gconn_variant* v, void* stream);
+
+/* ---------------------------------------------------------- incremental */
+/* Incremental connectivity (Section 3.5, Algorithm 3).  The handle owns a
+ * device-resident union-find over n vertices, initialised to singletons (an
+ * empty initial graph; insert a batch to start from a non-empty one).  Only
+ * root-based finish algorithms are allowed: the union-find rules, SV, and the
+ * Liu-Tarjan rule sets with RootUpdate; sampling must be NONE.
+ * Semantics (phase-concurrent, which Rem-CAS with splicing needs): a query
+ * batch sees exactly the union of all insert batches submitted before it on
+ * the handle; insert batches commute.  Calls on one handle must be ordered
+ * (same stream, or synchronised); the handle is not thread-safe.
+ * gconn_inc_create: *out receives the handle.  Errors: E_INVAL, E_UNSUPPORTED,
+ * E_NOMEM, E_CUDA. */
+typedef struct gconn_inc gconn_inc;
+gconn_status gconn_inc_create(uint32_t n, const gconn_variant* v, void* stream, gconn_inc** out);
+
+/* Insert b undirected edges (uint32[2b] pairs, device or host).  E_RANGE is
+ * reported through gconn_sync (or directly when the input is on the host). */
+gconn_status gconn_inc_insert_batch(gconn_inc* h, uint64_t b, const uint32_t* edges, void* stream);
+
+/* Answer q connectivity queries (Section 2): connected[i] = 1 iff pairs[2i]
+ * and pairs[2i+1] are in one component given every insert submitted before.
+ * pairs: uint32[2q]; connected: uint8[q] (device or host). */
+gconn_status gconn_inc_query(gconn_inc* h, uint64_t q, const uint32_t* pairs, uint8_t* connected,
+                             void* stream);
+
+/* Canonical min-id labels of the current state into uint32[n] (device or host). */
+gconn_status gconn_inc_labels(gconn_inc* h, uint32_t* labels, void* stream);
+
+/* Release the handle and its device memory (synchronises its last stream). */
+gconn_status gconn_inc_destroy(gconn_inc* h);
+
+/* ------------------------------------------------------------ utilities */
+/* Wait for `stream`, then return and clear the device error flags of the
+ * current device (GCONN_E_RANGE, GCONN_E_NONCONVERGED) or GCONN_E_CUDA. */
+gconn_status gconn_sync(void* stream);
+
+/* Static description of a status code. */
+const char* gconn_status_str(gconn_status s);
+
+/* Kernel launches made by this library in this process (all devices). */
+uint64_t gconn_launch_count(void);
+
+/* Per-kernel timing with CUDA events recorded on each launch's own stream.
+ * gconn_profile_enable(1) starts recording (0 stops), gconn_profile_reset
+ * clears the totals, gconn_profile_get(i, ...) synchronises pending events and
+ * returns the name, launch count and summed milliseconds of the i-th kernel
+ * (GCONN_E_INVAL once i is past the last one). */
+gconn_status gconn_profile_enable(int on);
+gconn_status gconn_profile_reset(void);
+gconn_status gconn_profile_get(int i, const char** name, uint64_t* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCONN_H */

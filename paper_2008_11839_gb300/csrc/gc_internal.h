@@ -1,0 +1,100 @@
+// gc_internal.h -- host-side helpers shared by the libgconn translation units:
+// status plumbing, pointer classification, stream-ordered scratch buffers,
+// occupancy-sized grids, and the launch wrapper that counts and (optionally)
+// times every kernel launch with CUDA events on the launching stream.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <utility>
+
+#include "../../include/gconn.h"
+
+namespace gc {
+
+constexpr uint32_t INF = 0xFFFFFFFFu;
+constexpr uint32_t ERR_RANGE = 1u;
+constexpr uint32_t ERR_NONCONV = 2u;
+constexpr uint32_t ERR_OVERFLOW = 4u;
+constexpr uint32_t DEFAULT_CAP = 1u << 24;
+constexpr uint64_t DEFAULT_SEED = 0x6C0A0001ull;
+
+// ------------------------------------------------------------------ status
+#define GC_CUDA(call)                                                             \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) return ::gc::cuda_status(e_);                      \
+    } while (0)
+#define GC_TRY(call)                                                              \
+    do {                                                                          \
+        gconn_status s_ = (call);                                                 \
+        if (s_ != GCONN_OK) return s_;                                            \
+    } while (0)
+
+gconn_status cuda_status(cudaError_t e);          // maps OOM -> E_NOMEM, else E_CUDA
+uint32_t* err_word();                             // device error word of the current device
+gconn_status read_and_clear_err(cudaStream_t st); // sync st, then read/clear the word
+
+// ----------------------------------------------------------------- devices
+int num_sms();                                    // SM count of the current device
+bool is_device_ptr(const void* p);                // device or managed memory
+
+// ------------------------------------------------------- scratch buffers
+// Stream-ordered device allocation: allocated and released on one stream.
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    gconn_status alloc(size_t bytes, cudaStream_t stream);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------ launching
+extern std::atomic<uint64_t> g_launches;
+extern std::atomic<bool> g_profiling;
+void prof_begin(const char* name, cudaStream_t st, void** token);
+void prof_end(void* token, cudaStream_t st);
+
+// Persistent-style grid: min(ceil(work / block), resident blocks on all SMs).
+template <class K>
+unsigned grid_for(K kernel, int block, uint64_t work, size_t smem = 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    uint64_t cap = (uint64_t)per_sm * (uint64_t)num_sms();
+    uint64_t need = (work + (uint64_t)block - 1) / (uint64_t)block;
+    if (need < 1) need = 1;
+    return (unsigned)(need < cap ? need : cap);
+}
+
+template <class... KArgs, class... Args>
+gconn_status launch(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                    cudaStream_t st, Args&&... args) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    void* tok = nullptr;
+    if (g_profiling.load(std::memory_order_relaxed)) prof_begin(name, st, &tok);
+    kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+    cudaError_t e = cudaGetLastError();
+    if (tok) prof_end(tok, st);
+    return e == cudaSuccess ? GCONN_OK : cuda_status(e);
+}
+
+// --------------------------------------------------------------- variant
+struct Variant {
+    int sample, k, hb_n, link, find, splice, lt_rules, block;
+    uint64_t seed;
+    uint32_t cap;
+};
+gconn_status resolve_variant(const gconn_variant* in, int input_kind, int want_forest, Variant* out);
+
+// Staging of possibly-host arrays onto the device.
+gconn_status stage_in(const void* src, size_t bytes, cudaStream_t st, DevBuf& buf, const void** dev);
+
+}  // namespace gc

@@ -1,0 +1,36 @@
+// gc_static.h -- internal interfaces between the static, BFS, rounds and
+// incremental translation units.
+#pragma once
+#include "gc_internal.h"
+#include "uf_device.cuh"
+
+namespace gc {
+
+void uf_triple(const Variant& v, int* L, int* F, int* S);
+UFState make_state(uint32_t n, uint32_t* P, uint32_t* H, u64w* W, uint32_t* sf, const Variant& v);
+gconn_status init_state(const UFState& s, cudaStream_t st);
+gconn_status union_coo(const Variant& v, const UFState& s, const uint32_t* edges, uint64_t m, uint32_t eid_base,
+                       cudaStream_t st);
+gconn_status compress_all(const Variant& v, const UFState& s, cudaStream_t st);
+gconn_status finalize_labels(const Variant& v, const UFState& s, uint32_t* labels, cudaStream_t st);
+gconn_status sf_output(uint32_t n, const uint32_t* sf, uint64_t* forest, uint64_t* count, cudaStream_t st);
+
+// BFS sampling (Algorithm 4): labels the source's component with its minimum
+// id (in P, or in W for Union-JTB), records BFS-tree arcs in s.sf, and writes
+// that minimum as L_max.
+gconn_status bfs_sample(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,
+                        uint32_t* lmax_dev, cudaStream_t st);
+
+// Round-based finishes (Shiloach-Vishkin, Liu-Tarjan) over a COO list with
+// optional per-edge forest ids (NULL = the edge index).  P ends fully
+// compressed and min-rooted.
+gconn_status rounds_coo(const Variant& v, const UFState& s, const uint32_t* edges, const uint32_t* eids,
+                        uint64_t m, cudaStream_t st);
+
+// The same over the arcs of the active CSR vertices gathered by k_vg.
+gconn_status rounds_csr(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,
+                        const uint32_t* active, const uint32_t* small, const uint32_t* nsmall,
+                        const unsigned long long* tasks, const uint32_t* ntasks, uint32_t task_cap,
+                        const uint32_t* over, const uint32_t* nover, cudaStream_t st);
+
+}  // namespace gc

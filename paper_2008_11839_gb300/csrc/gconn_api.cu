@@ -1,0 +1,308 @@
+// gconn_api.cu -- status codes, the per-device error word, pointer checks,
+// stream-ordered scratch, kernel-launch accounting and timing, and variant
+// validation for libgconn.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gc_internal.h"
+
+// Device error word: bit 0 = endpoint out of range, bit 1 = iteration cap
+// reached, bit 2 = a size limit was exceeded.  One per device.
+__device__ uint32_t g_gconn_err;
+
+namespace gc {
+
+std::atomic<uint64_t> g_launches{0};
+std::atomic<bool> g_profiling{false};
+
+gconn_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return GCONN_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return GCONN_E_NOMEM;
+    }
+    return GCONN_E_CUDA;
+}
+
+static std::mutex g_mu;
+static constexpr int MAX_DEV = 64;
+static uint32_t* g_err_ptr[MAX_DEV];
+static int g_sms[MAX_DEV];
+
+uint32_t* err_word() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= MAX_DEV) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_err_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_gconn_err) != cudaSuccess) return nullptr;
+        g_err_ptr[dev] = (uint32_t*)p;
+    }
+    return g_err_ptr[dev];
+}
+
+int num_sms() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= MAX_DEV) return 1;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_sms[dev]) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g_sms[dev] = sms > 0 ? sms : 1;
+    }
+    return g_sms[dev];
+}
+
+gconn_status read_and_clear_err(cudaStream_t st) {
+    GC_CUDA(cudaStreamSynchronize(st));
+    uint32_t* p = err_word();
+    if (!p) return GCONN_E_CUDA;
+    uint32_t h = 0;
+    GC_CUDA(cudaMemcpy(&h, p, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (h) {
+        uint32_t z = 0;
+        GC_CUDA(cudaMemcpy(p, &z, sizeof(uint32_t), cudaMemcpyHostToDevice));
+    }
+    if (h & ERR_RANGE) return GCONN_E_RANGE;
+    if (h & ERR_NONCONV) return GCONN_E_NONCONVERGED;
+    if (h & ERR_OVERFLOW) return GCONN_E_INVAL;
+    return GCONN_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+gconn_status DevBuf::alloc(size_t bytes, cudaStream_t stream) {
+    release();
+    st = stream;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        return cuda_status(e);
+    }
+    return GCONN_OK;
+}
+
+void DevBuf::release() {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+}
+
+gconn_status stage_in(const void* src, size_t bytes, cudaStream_t st, DevBuf& buf, const void** dev) {
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return GCONN_OK;
+    }
+    GC_TRY(buf.alloc(bytes, st));
+    GC_CUDA(cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, st));
+    *dev = buf.p;
+    return GCONN_OK;
+}
+
+// ------------------------------------------------------------- profiling
+struct PendingRec {
+    std::string name;
+    cudaEvent_t a, b;
+};
+struct Total {
+    uint64_t launches = 0;
+    double ms = 0;
+};
+static std::mutex g_pmu;
+static std::vector<PendingRec> g_pending;
+static std::vector<cudaEvent_t> g_event_pool;
+static std::vector<std::string> g_order;
+static std::map<std::string, Total> g_totals;
+
+static cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(const char* name, cudaStream_t st, void** token) {
+    std::lock_guard<std::mutex> lk(g_pmu);
+    PendingRec* r = new PendingRec{name, take_event(), take_event()};
+    cudaEventRecord(r->a, st);
+    *token = r;
+}
+
+void prof_end(void* token, cudaStream_t st) {
+    PendingRec* r = (PendingRec*)token;
+    cudaEventRecord(r->b, st);
+    std::lock_guard<std::mutex> lk(g_pmu);
+    g_pending.push_back(*r);
+    delete r;
+}
+
+static void prof_collect() {
+    std::lock_guard<std::mutex> lk(g_pmu);
+    for (auto& r : g_pending) {
+        float ms = 0;
+        cudaEventSynchronize(r.b);
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        if (!g_totals.count(r.name)) g_order.push_back(r.name);
+        Total& t = g_totals[r.name];
+        t.launches++;
+        t.ms += ms;
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+    }
+    g_pending.clear();
+}
+
+// ---------------------------------------------------------------- variants
+gconn_status resolve_variant(const gconn_variant* in, int input_kind, int want_forest, Variant* out) {
+    gconn_variant d;
+    gconn_variant_default(&d);
+    if (in) d = *in;
+    if (input_kind == 0 && !in) d.sample = GCONN_SAMPLE_NONE;
+    gconn_status s = gconn_variant_check(&d, input_kind, want_forest);
+    if (s != GCONN_OK) return s;
+    out->sample = d.sample;
+    out->k = d.k > 0 ? d.k : 2;
+    out->hb_n = d.hb_n > 0 ? d.hb_n : 4;
+    out->link = d.link;
+    out->find = d.find;
+    out->splice = d.splice;
+    out->lt_rules = d.lt_rules;
+    out->block = d.block;
+    out->seed = d.seed;
+    out->cap = d.iter_cap ? d.iter_cap : DEFAULT_CAP;
+    return GCONN_OK;
+}
+
+}  // namespace gc
+
+using namespace gc;
+
+static bool lt_valid(int r) {
+    // the 16 rule sets of the appendix list
+    static const int ok[] = {
+        GCONN_LT_CONNECT | GCONN_LT_ALTER,                                                    // CUSA
+        GCONN_LT_CONNECT | GCONN_LT_ROOTUPDATE | GCONN_LT_ALTER,                              // CRSA
+        GCONN_LT_PARENT | GCONN_LT_ALTER,                                                     // PUSA
+        GCONN_LT_PARENT | GCONN_LT_ROOTUPDATE | GCONN_LT_ALTER,                               // PRSA
+        GCONN_LT_PARENT,                                                                      // PUS
+        GCONN_LT_PARENT | GCONN_LT_ROOTUPDATE,                                                // PRS
+        GCONN_LT_EXTENDED | GCONN_LT_ALTER,                                                   // EUSA
+        GCONN_LT_EXTENDED,                                                                    // EUS
+        GCONN_LT_CONNECT | GCONN_LT_FULLSHORTCUT | GCONN_LT_ALTER,                            // CUFA
+        GCONN_LT_CONNECT | GCONN_LT_ROOTUPDATE | GCONN_LT_FULLSHORTCUT | GCONN_LT_ALTER,      // CRFA
+        GCONN_LT_PARENT | GCONN_LT_FULLSHORTCUT | GCONN_LT_ALTER,                             // PUFA
+        GCONN_LT_PARENT | GCONN_LT_ROOTUPDATE | GCONN_LT_FULLSHORTCUT | GCONN_LT_ALTER,       // PRFA
+        GCONN_LT_PARENT | GCONN_LT_FULLSHORTCUT,                                              // PUF
+        GCONN_LT_PARENT | GCONN_LT_ROOTUPDATE | GCONN_LT_FULLSHORTCUT,                        // PRF
+        GCONN_LT_EXTENDED | GCONN_LT_FULLSHORTCUT | GCONN_LT_ALTER,                           // EUFA
+        GCONN_LT_EXTENDED | GCONN_LT_FULLSHORTCUT,                                            // EUF
+    };
+    for (int x : ok)
+        if (x == r) return true;
+    return false;
+}
+
+extern "C" gconn_status gconn_variant_default(gconn_variant* v) {
+    if (!v) return GCONN_E_INVAL;
+    memset(v, 0, sizeof(*v));
+    v->sample = GCONN_SAMPLE_KOUT;
+    v->k = 2;
+    v->hb_n = 4;
+    v->link = GCONN_LINK_ASYNC;
+    v->find = GCONN_FIND_NAIVE;
+    v->splice = GCONN_SPLICE_NONE;
+    v->lt_rules = GCONN_LT_PARENT | GCONN_LT_ROOTUPDATE | GCONN_LT_FULLSHORTCUT;
+    v->block = 0;
+    v->seed = DEFAULT_SEED;
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_variant_check(const gconn_variant* v, int input_kind, int want_forest) {
+    if (!v) return GCONN_E_INVAL;
+    if (input_kind != 0 && input_kind != 1) return GCONN_E_INVAL;
+    if (v->reserved != 0) return GCONN_E_INVAL;
+    if (v->sample < 0 || v->sample > GCONN_SAMPLE_BFS) return GCONN_E_INVAL;
+    if (v->link < 0 || v->link > GCONN_LINK_LT) return GCONN_E_INVAL;
+    if (v->find < 0 || v->find > GCONN_FIND_FULLSHORTCUT) return GCONN_E_INVAL;
+    if (v->splice < 0 || v->splice > GCONN_SPLICE_SPLICE) return GCONN_E_INVAL;
+    if (v->k < 0 || v->hb_n < 0 || v->k > 1024 || v->hb_n > 1024) return GCONN_E_INVAL;
+    if (v->block != 0 && (v->block < 64 || v->block > 1024 || v->block % 32 != 0)) return GCONN_E_INVAL;
+    if (v->sample != GCONN_SAMPLE_NONE && input_kind == 0) return GCONN_E_UNSUPPORTED;
+    bool rem = v->link == GCONN_LINK_REMCAS, jtb = v->link == GCONN_LINK_JTB;
+    if (v->splice != GCONN_SPLICE_NONE && !rem) return GCONN_E_UNSUPPORTED;
+    if (v->find == GCONN_FIND_TWOTRYSPLIT && !jtb) return GCONN_E_UNSUPPORTED;
+    if (rem && v->find == GCONN_FIND_COMPRESS) return GCONN_E_UNSUPPORTED;
+    if (jtb && v->find != GCONN_FIND_NAIVE && v->find != GCONN_FIND_TWOTRYSPLIT &&
+        v->find != GCONN_FIND_FULLSHORTCUT)
+        return GCONN_E_UNSUPPORTED;
+    if (v->link == GCONN_LINK_SV && v->find != GCONN_FIND_NAIVE && v->find != GCONN_FIND_FULLSHORTCUT)
+        return GCONN_E_UNSUPPORTED;
+    if (v->link == GCONN_LINK_LT) {
+        if (!lt_valid(v->lt_rules)) return GCONN_E_UNSUPPORTED;
+        if (v->find != GCONN_FIND_NAIVE && v->find != GCONN_FIND_FULLSHORTCUT) return GCONN_E_UNSUPPORTED;
+        if (want_forest && !(v->lt_rules & GCONN_LT_ROOTUPDATE)) return GCONN_E_UNSUPPORTED;
+    }
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_sync(void* stream) { return read_and_clear_err((cudaStream_t)stream); }
+
+extern "C" const char* gconn_status_str(gconn_status s) {
+    switch (s) {
+        case GCONN_OK: return "ok";
+        case GCONN_E_INVAL: return "invalid argument";
+        case GCONN_E_RANGE: return "vertex id out of range";
+        case GCONN_E_NOMEM: return "device out of memory";
+        case GCONN_E_UNSUPPORTED: return "unsupported variant combination";
+        case GCONN_E_NONCONVERGED: return "iteration cap reached";
+        case GCONN_E_CUDA: return "CUDA runtime error";
+    }
+    return "unknown status";
+}
+
+extern "C" uint64_t gconn_launch_count(void) { return g_launches.load(); }
+
+extern "C" gconn_status gconn_profile_enable(int on) {
+    g_profiling.store(on != 0);
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_profile_reset(void) {
+    prof_collect();
+    std::lock_guard<std::mutex> lk(g_pmu);
+    g_totals.clear();
+    g_order.clear();
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_profile_get(int i, const char** name, uint64_t* launches, double* total_ms) {
+    prof_collect();
+    std::lock_guard<std::mutex> lk(g_pmu);
+    if (i < 0 || i >= (int)g_order.size()) return GCONN_E_INVAL;
+    const std::string& k = g_order[i];
+    const Total& t = g_totals[k];
+    if (name) *name = k.c_str();
+    if (launches) *launches = t.launches;
+    if (total_ms) *total_ms = t.ms;
+    return GCONN_OK;
+}

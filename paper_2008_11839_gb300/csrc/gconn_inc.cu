@@ -1,0 +1,192 @@
+// gconn_inc.cu -- incremental connectivity (Section 3.5, Algorithm 3): a
+// device-resident union-find that absorbs batches of edge insertions and
+// answers batches of connectivity queries.  Old batches are never re-read:
+// every finish algorithm allowed here is root-based, so the forest alone
+// carries the connectivity of everything inserted so far.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gc_internal.h"
+#include "gc_static.h"
+#include "static_kernels.cuh"
+
+using namespace gc;
+
+struct gconn_inc {
+    uint32_t n;
+    int device;
+    Variant v;
+    uint32_t* P;
+    uint32_t* H;
+    u64w* W;
+    cudaStream_t last;
+};
+
+namespace gc {
+
+// Query batch: find both endpoints (with the handle's find rule, which may
+// compress) and compare the roots.
+template <int L, int F>
+__global__ void __launch_bounds__(256) k_query(const uint2* __restrict__ Q, uint64_t q, UFState s, uint8_t* out) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < q; i += stride) {
+        uint2 e = __ldcs(Q + i);
+        if (e.x >= s.n || e.y >= s.n) {
+            atomicOr(s.err, GC_DERR_RANGE);
+            out[i] = 0;
+            continue;
+        }
+        Spin sp(s.cap);
+        uint32_t a, b;
+        if (L == LK_JTB) {
+            a = jtb_find<F>(s, e.x, sp);
+            b = jtb_find<F>(s, e.y, sp);
+        } else {
+            a = uf_find<F>(s, e.x, sp);
+            b = uf_find<F>(s, e.y, sp);
+        }
+        out[i] = (a == b) ? 1 : 0;
+    }
+}
+
+template <int L, int F>
+static gconn_status launch_query(const UFState& s, const uint2* Q, uint64_t q, uint8_t* out, int block,
+                                 cudaStream_t st) {
+    auto k = k_query<L, F>;
+    return launch("query", k, grid_for(k, block, q), block, 0, st, Q, q, s, out);
+}
+
+static gconn_status query_dispatch(const Variant& v, const UFState& s, const uint2* Q, uint64_t q, uint8_t* out,
+                                   cudaStream_t st) {
+    int L, F, S;
+    if (v.link == GCONN_LINK_SV || v.link == GCONN_LINK_LT) {
+        L = LK_ASYNC;
+        F = FD_NAIVE;
+    } else {
+        uf_triple(v, &L, &F, &S);
+    }
+    int B = v.block > 0 ? v.block : 256;
+    if (L == LK_JTB) return F == FD_TWOTRY ? launch_query<LK_JTB, FD_TWOTRY>(s, Q, q, out, B, st)
+                                           : launch_query<LK_JTB, FD_NAIVE>(s, Q, q, out, B, st);
+    switch (F) {
+        case FD_COMPRESS: return launch_query<LK_ASYNC, FD_COMPRESS>(s, Q, q, out, B, st);
+        case FD_SPLIT: return launch_query<LK_ASYNC, FD_SPLIT>(s, Q, q, out, B, st);
+        case FD_HALVE: return launch_query<LK_ASYNC, FD_HALVE>(s, Q, q, out, B, st);
+        default: return launch_query<LK_ASYNC, FD_NAIVE>(s, Q, q, out, B, st);
+    }
+}
+
+static UFState handle_state(gconn_inc* h) { return make_state(h->n, h->P, h->H, h->W, nullptr, h->v); }
+
+}  // namespace gc
+
+extern "C" gconn_status gconn_inc_create(uint32_t n, const gconn_variant* vin, void* stream, gconn_inc** out) {
+    if (!out || n == 0xFFFFFFFFu) return GCONN_E_INVAL;
+    *out = nullptr;
+    gconn_variant d;
+    gconn_variant_default(&d);
+    if (vin) d = *vin;
+    else d.sample = GCONN_SAMPLE_NONE;
+    if (d.sample != GCONN_SAMPLE_NONE) return GCONN_E_UNSUPPORTED;   // batches are COO
+    Variant v;
+    GC_TRY(resolve_variant(&d, 0, 1, &v));
+    cudaStream_t st = (cudaStream_t)stream;
+    gconn_inc* h = new gconn_inc();
+    h->n = n;
+    h->v = v;
+    h->last = st;
+    cudaGetDevice(&h->device);
+    size_t cnt = n ? n : 1;
+    cudaError_t e = cudaMalloc(&h->P, sizeof(uint32_t) * cnt);
+    if (e == cudaSuccess && v.link == GCONN_LINK_HOOKS) e = cudaMalloc(&h->H, sizeof(uint32_t) * cnt);
+    if (e == cudaSuccess && v.link == GCONN_LINK_JTB) e = cudaMalloc(&h->W, sizeof(u64w) * cnt);
+    if (e != cudaSuccess) {
+        gconn_inc_destroy(h);
+        return cuda_status(e);
+    }
+    gconn_status s = init_state(handle_state(h), st);
+    if (s != GCONN_OK) {
+        gconn_inc_destroy(h);
+        return s;
+    }
+    *out = h;
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_inc_insert_batch(gconn_inc* h, uint64_t b, const uint32_t* edges, void* stream) {
+    if (!h || (b && !edges) || b >= (1ull << 63) || ((uintptr_t)edges & 7u)) return GCONN_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last = st;
+    if (b == 0) return GCONN_OK;
+    if (h->n == 0) return GCONN_E_RANGE;
+    DevBuf eb;
+    const uint32_t* de = nullptr;
+    bool host = !is_device_ptr(edges);
+    GC_TRY(stage_in(edges, sizeof(uint32_t) * 2 * b, st, eb, (const void**)&de));
+    UFState s = handle_state(h);
+    if (h->v.link == GCONN_LINK_SV || h->v.link == GCONN_LINK_LT) {
+        GC_TRY(rounds_coo(h->v, s, de, nullptr, b, st));
+    } else {
+        GC_TRY(union_coo(h->v, s, de, b, 0, st));
+    }
+    if (host) return read_and_clear_err(st);
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_inc_query(gconn_inc* h, uint64_t q, const uint32_t* pairs, uint8_t* connected,
+                                        void* stream) {
+    if (!h || (q && (!pairs || !connected)) || q >= (1ull << 63) || ((uintptr_t)pairs & 7u)) return GCONN_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last = st;
+    if (q == 0) return GCONN_OK;
+    if (h->n == 0) return GCONN_E_RANGE;
+    DevBuf pb, ob;
+    const uint32_t* dp = nullptr;
+    bool host_in = !is_device_ptr(pairs), host_out = !is_device_ptr(connected);
+    GC_TRY(stage_in(pairs, sizeof(uint32_t) * 2 * q, st, pb, (const void**)&dp));
+    uint8_t* dout = connected;
+    if (host_out) {
+        GC_TRY(ob.alloc(q, st));
+        dout = ob.as<uint8_t>();
+    }
+    GC_TRY(query_dispatch(h->v, handle_state(h), (const uint2*)dp, q, dout, st));
+    if (host_out) GC_CUDA(cudaMemcpyAsync(connected, dout, q, cudaMemcpyDeviceToHost, st));
+    if (host_in || host_out) return read_and_clear_err(st);
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_inc_labels(gconn_inc* h, uint32_t* labels, void* stream) {
+    if (!h || (h->n && !labels)) return GCONN_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last = st;
+    if (h->n == 0) return GCONN_OK;
+    bool host = !is_device_ptr(labels);
+    DevBuf lb;
+    uint32_t* dl = labels;
+    if (host) {
+        GC_TRY(lb.alloc(sizeof(uint32_t) * (size_t)h->n, st));
+        dl = lb.as<uint32_t>();
+    }
+    Variant fv = h->v;
+    if (fv.link == GCONN_LINK_SV || fv.link == GCONN_LINK_LT) fv.link = GCONN_LINK_ASYNC;
+    GC_TRY(finalize_labels(fv, handle_state(h), dl, st));
+    if (host) {
+        GC_CUDA(cudaMemcpyAsync(labels, dl, sizeof(uint32_t) * (size_t)h->n, cudaMemcpyDeviceToHost, st));
+        return read_and_clear_err(st);
+    }
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_inc_destroy(gconn_inc* h) {
+    if (!h) return GCONN_E_INVAL;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->last);
+    if (h->P) cudaFree(h->P);
+    if (h->H) cudaFree(h->H);
+    if (h->W) cudaFree(h->W);
+    cudaSetDevice(prev);
+    delete h;
+    return GCONN_OK;
+}

@@ -1,0 +1,362 @@
+// gconn_static.cu -- host orchestration of static connectivity and spanning
+// forest (Algorithms 1 and 2) over COO and CSR input.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "gc_internal.h"
+#include "gc_static.h"
+#include "static_kernels.cuh"
+
+namespace gc {
+
+// Every normalised (link, find, splice) triple the library instantiates.
+// Calls fn.template operator()<L, F, S, SF>().
+template <class Fn>
+gconn_status dispatch_uf(int L, int F, int S, bool SF, Fn&& fn) {
+#define GC_UF_CASE(l, f, s)                                                              \
+    if (L == l && F == f && S == s)                                                      \
+        return SF ? fn.template operator()<l, f, s, true>() : fn.template operator()<l, f, s, false>();
+    GC_UF_CASE(LK_ASYNC, FD_NAIVE, SP_NONE)
+    GC_UF_CASE(LK_ASYNC, FD_COMPRESS, SP_NONE)
+    GC_UF_CASE(LK_ASYNC, FD_SPLIT, SP_NONE)
+    GC_UF_CASE(LK_ASYNC, FD_HALVE, SP_NONE)
+    GC_UF_CASE(LK_HOOKS, FD_NAIVE, SP_NONE)
+    GC_UF_CASE(LK_HOOKS, FD_COMPRESS, SP_NONE)
+    GC_UF_CASE(LK_HOOKS, FD_SPLIT, SP_NONE)
+    GC_UF_CASE(LK_HOOKS, FD_HALVE, SP_NONE)
+    GC_UF_CASE(LK_EARLY, FD_NAIVE, SP_NONE)
+    GC_UF_CASE(LK_EARLY, FD_COMPRESS, SP_NONE)
+    GC_UF_CASE(LK_EARLY, FD_SPLIT, SP_NONE)
+    GC_UF_CASE(LK_EARLY, FD_HALVE, SP_NONE)
+    GC_UF_CASE(LK_REMCAS, FD_NAIVE, SP_SPLIT_ONE)
+    GC_UF_CASE(LK_REMCAS, FD_NAIVE, SP_HALVE_ONE)
+    GC_UF_CASE(LK_REMCAS, FD_NAIVE, SP_SPLICE)
+    GC_UF_CASE(LK_REMCAS, FD_SPLIT, SP_SPLIT_ONE)
+    GC_UF_CASE(LK_REMCAS, FD_SPLIT, SP_HALVE_ONE)
+    GC_UF_CASE(LK_REMCAS, FD_SPLIT, SP_SPLICE)
+    GC_UF_CASE(LK_REMCAS, FD_HALVE, SP_SPLIT_ONE)
+    GC_UF_CASE(LK_REMCAS, FD_HALVE, SP_HALVE_ONE)
+    GC_UF_CASE(LK_REMCAS, FD_HALVE, SP_SPLICE)
+    GC_UF_CASE(LK_JTB, FD_NAIVE, SP_NONE)
+    GC_UF_CASE(LK_JTB, FD_TWOTRY, SP_NONE)
+#undef GC_UF_CASE
+    return GCONN_E_UNSUPPORTED;
+}
+
+// Map the public variant onto the instantiated triple.
+void uf_triple(const Variant& v, int* L, int* F, int* S) {
+    *L = v.link;
+    int f = v.find;
+    if (f == GCONN_FIND_FULLSHORTCUT) f = GCONN_FIND_NAIVE;
+    *F = f == GCONN_FIND_COMPRESS ? FD_COMPRESS
+       : f == GCONN_FIND_SPLIT ? FD_SPLIT
+       : f == GCONN_FIND_HALVE ? FD_HALVE
+       : f == GCONN_FIND_TWOTRYSPLIT ? FD_TWOTRY : FD_NAIVE;
+    *S = SP_NONE;
+    if (v.link == GCONN_LINK_REMCAS)
+        *S = v.splice == GCONN_SPLICE_SPLIT_ONE ? SP_SPLIT_ONE
+           : v.splice == GCONN_SPLICE_HALVE_ONE ? SP_HALVE_ONE : SP_SPLICE;
+}
+
+static int block_of(const Variant& v) { return v.block > 0 ? v.block : 256; }
+
+UFState make_state(uint32_t n, uint32_t* P, uint32_t* H, u64w* W, uint32_t* sf, const Variant& v) {
+    UFState s;
+    s.P = P; s.H = H; s.W = W; s.sf = sf;
+    s.err = err_word();
+    s.n = n;
+    s.cap = v.cap;
+    s.seed = (uint32_t)(v.seed ^ (v.seed >> 32));
+    return s;
+}
+
+gconn_status init_state(const UFState& s, cudaStream_t st) {
+    if (s.n == 0) return GCONN_OK;
+    return launch("init", k_init, grid_for(k_init, 256, s.n), 256, 0, st, s.n, s.P, s.H, s.W, s.sf);
+}
+
+gconn_status union_coo(const Variant& v, const UFState& s, const uint32_t* edges, uint64_t m,
+                       uint32_t eid_base, cudaStream_t st) {
+    if (m == 0) return GCONN_OK;
+    int L, F, S;
+    uf_triple(v, &L, &F, &S);
+    int B = block_of(v);
+    return dispatch_uf(L, F, S, s.sf != nullptr, [&]<int l, int f, int sp, bool sf>() {
+        auto k = k_union_coo<l, f, sp, sf>;
+        return launch("union_coo", k, grid_for(k, B, m), B, 0, st, (const uint2*)edges, m, s, eid_base);
+    });
+}
+
+gconn_status compress_all(const Variant& v, const UFState& s, cudaStream_t st) {
+    if (s.n == 0) return GCONN_OK;
+    if (v.link == GCONN_LINK_JTB)
+        return launch("compress", k_compress<LK_JTB>, grid_for(k_compress<LK_JTB>, 256, s.n), 256, 0, st, s);
+    return launch("compress", k_compress<LK_ASYNC>, grid_for(k_compress<LK_ASYNC>, 256, s.n), 256, 0, st, s);
+}
+
+gconn_status finalize_labels(const Variant& v, const UFState& s, uint32_t* labels, cudaStream_t st) {
+    if (s.n == 0) return GCONN_OK;
+    unsigned g = grid_for(k_finalize, 256, s.n);
+    if (v.link != GCONN_LINK_JTB) {
+        // labels may alias P: the walk then compresses in place
+        return launch("finalize", k_finalize, g, 256, 0, st, s, labels);
+    }
+    GC_TRY(compress_all(v, s, st));
+    GC_TRY(launch("jtb_fill", k_fill, g, 256, 0, st, s.n, labels, INF));
+    GC_TRY(launch("jtb_min", k_jtb_min, g, 256, 0, st, s, labels));
+    return launch("jtb_gather", k_jtb_gather, g, 256, 0, st, s, labels);
+}
+
+gconn_status sf_output(uint32_t n, const uint32_t* sf, uint64_t* forest, uint64_t* count, cudaStream_t st) {
+    bool forest_dev = is_device_ptr(forest), count_dev = is_device_ptr(count);
+    DevBuf fbuf, cbuf;
+    unsigned long long* f = (unsigned long long*)forest;
+    unsigned long long* c = (unsigned long long*)count;
+    if (!forest_dev) { GC_TRY(fbuf.alloc(sizeof(uint64_t) * (size_t)(n ? n : 1), st)); f = fbuf.as<unsigned long long>(); }
+    if (!count_dev) { GC_TRY(cbuf.alloc(sizeof(uint64_t), st)); c = cbuf.as<unsigned long long>(); }
+    GC_CUDA(cudaMemsetAsync(c, 0, sizeof(uint64_t), st));
+    if (n) GC_TRY(launch("sf_compact", k_sf_compact, grid_for(k_sf_compact, 256, n), 256, 0, st, n, sf, f, c));
+    if (!forest_dev || !count_dev) {
+        uint64_t hc = 0;
+        GC_CUDA(cudaMemcpyAsync(&hc, c, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        GC_CUDA(cudaStreamSynchronize(st));
+        if (!count_dev) *count = hc;
+        if (!forest_dev && hc)
+            GC_CUDA(cudaMemcpyAsync(forest, f, sizeof(uint64_t) * hc, cudaMemcpyDeviceToHost, st));
+    }
+    return GCONN_OK;
+}
+
+// ---------------------------------------------------------------- CSR path
+struct CsrScratch {
+    DevBuf lmax, counters, active, small, tasks, over;
+};
+
+gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,
+                        uint32_t* lmax_dev, cudaStream_t st) {
+    uint32_t n = s.n;
+    int L, F, S;
+    uf_triple(v, &L, &F, &S);
+    int B = block_of(v);
+    bool sf = s.sf != nullptr;
+    bool jtb = v.link == GCONN_LINK_JTB;
+    if (v.sample == GCONN_SAMPLE_KOUT) {
+        GC_TRY(dispatch_uf(L, F, S, sf, [&]<int l, int f, int sp, bool w>() {
+            auto k = k_kout<l, f, sp, w>;
+            return launch("kout", k, grid_for(k, B, n), B, 0, st, off, cols, v.k, s);
+        }));
+    } else if (v.sample == GCONN_SAMPLE_HB) {
+        GC_TRY(launch("hb1", k_hb1, grid_for(k_hb1, 256, n), 256, 0, st, off, cols, n, s.P, s.sf, s.err));
+        if (jtb) {
+            UFState sp = s;
+            sp.W = nullptr;
+            GC_TRY(launch("compress", k_compress<LK_ASYNC>, grid_for(k_compress<LK_ASYNC>, 256, n), 256, 0, st, sp));
+            GC_TRY(launch("w_from_p", k_w_from_p, grid_for(k_w_from_p, 256, n), 256, 0, st, n, s.P, s.W));
+        }
+        GC_TRY(dispatch_uf(L, F, S, sf, [&]<int l, int f, int sp, bool w>() {
+            auto k = k_hb2<l, f, sp, w>;
+            return launch("hb2", k, grid_for(k, B, n), B, 0, st, off, cols, v.hb_n, s);
+        }));
+    } else if (v.sample == GCONN_SAMPLE_BFS) {
+        return bfs_sample(v, s, off, cols, lmax_dev, st);   // also yields L_max
+    }
+    GC_TRY(compress_all(v, s, st));
+    if (jtb)
+        return launch("lmax", k_lmax<LK_JTB>, 1, LMAX_SAMPLES, 0, st, s, v.seed, lmax_dev);
+    return launch("lmax", k_lmax<LK_ASYNC>, 1, LMAX_SAMPLES, 0, st, s, v.seed, lmax_dev);
+}
+
+// Runs the sampling phase (unless NONE), L_max, vertex gathering and the
+// finish phase of Algorithm 1 on CSR.  Leaves P (or W) final, not finalised.
+gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,
+                         cudaStream_t st) {
+    uint32_t n = s.n;
+    if (n == 0) return GCONN_OK;
+    CsrScratch sc;
+    bool sampled = v.sample != GCONN_SAMPLE_NONE;
+    uint32_t* lmax = nullptr;
+    // the rounds-based finishes (SV, LT) sample with Union-Async
+    Variant sv = v;
+    bool rounds = v.link == GCONN_LINK_SV || v.link == GCONN_LINK_LT;
+    if (rounds) { sv.link = GCONN_LINK_ASYNC; sv.find = GCONN_FIND_NAIVE; sv.splice = 0; }
+    if (sampled) {
+        GC_TRY(sc.lmax.alloc(sizeof(uint32_t), st));
+        lmax = sc.lmax.as<uint32_t>();
+        GC_TRY(csr_sample(sv, s, off, cols, lmax, st));
+    }
+    // vertex gathering
+    uint64_t task_cap = (uint64_t)n + 1024;
+    GC_TRY(sc.counters.alloc(4 * sizeof(uint32_t), st));
+    uint32_t* cnt = sc.counters.as<uint32_t>();
+    GC_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(uint32_t), st));
+    uint32_t* active = nullptr;
+    if (sampled) {
+        GC_TRY(sc.active.alloc(sizeof(uint32_t) * (((size_t)n + 31) / 32), st));
+        active = sc.active.as<uint32_t>();
+    }
+    GC_TRY(sc.small.alloc(sizeof(uint32_t) * (size_t)n, st));
+    GC_TRY(sc.tasks.alloc(sizeof(unsigned long long) * task_cap, st));
+    GC_TRY(sc.over.alloc(sizeof(uint32_t) * (size_t)n, st));
+    uint32_t* small = sc.small.as<uint32_t>();
+    unsigned long long* tasks = sc.tasks.as<unsigned long long>();
+    uint32_t* over = sc.over.as<uint32_t>();
+    bool jtb = sv.link == GCONN_LINK_JTB;
+    {
+        auto k = jtb ? k_vg<LK_JTB> : k_vg<LK_ASYNC>;
+        GC_TRY(launch("vg", k, grid_for(k, 256, (uint64_t)n), 256, 0, st, off, s, lmax, active, small, cnt + 0,
+                      tasks, (uint32_t)task_cap, cnt + 1, over, cnt + 2));
+    }
+    if (rounds) return rounds_csr(v, s, off, cols, active, small, cnt + 0, tasks, cnt + 1, (uint32_t)task_cap,
+                                  over, cnt + 2, st);
+    int L, F, S;
+    uf_triple(v, &L, &F, &S);
+    int B = block_of(v);
+    return dispatch_uf(L, F, S, s.sf != nullptr, [&]<int l, int f, int sp, bool w>() {
+        auto k1 = k_finish_small<l, f, sp, w>;
+        GC_TRY(launch("finish_small", k1, grid_for(k1, B, n), B, 0, st, off, cols, s, active, small, cnt + 0));
+        auto k2 = k_finish_tasks<l, f, sp, w>;
+        GC_TRY(launch("finish_tasks", k2, grid_for(k2, B, (uint64_t)n * 32), B, 0, st, off, cols, s, active,
+                      tasks, cnt + 1, (uint32_t)task_cap));
+        auto k3 = k_finish_over<l, f, sp, w>;
+        return launch("finish_over", k3, grid_for(k3, B, (uint64_t)n * B), B, 0, st, off, cols, s, active, over,
+                      cnt + 2);
+    });
+}
+
+// --------------------------------------------------------------- drivers
+static gconn_status static_run(uint32_t n, uint64_t m, const uint32_t* edges, const uint64_t* off,
+                               const uint32_t* cols, uint32_t* labels, uint64_t* forest, uint64_t* forest_count,
+                               const gconn_variant* vin, int want_forest, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    bool csr = off != nullptr;
+    if (n == 0xFFFFFFFFu) return GCONN_E_INVAL;
+    Variant v;
+    GC_TRY(resolve_variant(vin, csr ? 1 : 0, want_forest, &v));
+    if (want_forest && (!forest || !forest_count)) return GCONN_E_INVAL;
+    if (!want_forest && !labels && n) return GCONN_E_INVAL;
+    if (csr && (!off || (!cols && n))) return GCONN_E_INVAL;
+    if (!csr && m && !edges) return GCONN_E_INVAL;
+    if (!csr && want_forest && m >= 0xFFFFFFFFull) return GCONN_E_INVAL;
+    if (!csr && m >= (1ull << 63)) return GCONN_E_INVAL;
+    // edges are read as 8-byte pairs, offsets as 8-byte words
+    if (!csr && edges && ((uintptr_t)edges & 7u)) return GCONN_E_INVAL;
+    if (csr && ((uintptr_t)off & 7u)) return GCONN_E_INVAL;
+    if (csr && cols && ((uintptr_t)cols & 3u)) return GCONN_E_INVAL;
+    if (n == 0) {
+        if (!csr && m) return GCONN_E_RANGE;
+        if (want_forest) {
+            uint64_t z = 0;
+            if (is_device_ptr(forest_count)) GC_CUDA(cudaMemcpyAsync(forest_count, &z, 8, cudaMemcpyHostToDevice, st));
+            else *forest_count = 0;
+        }
+        return GCONN_OK;
+    }
+    int dev = 0;
+    GC_CUDA(cudaGetDevice(&dev));
+    (void)dev;
+
+    // stage inputs
+    DevBuf ebuf, obuf, cbuf, lbuf, pbuf, hbuf, wbuf, sfbuf;
+    const uint32_t* d_edges = edges;
+    const uint64_t* d_off = off;
+    const uint32_t* d_cols = cols;
+    bool any_host = false;
+    if (!csr) {
+        if (m) {
+            bool h = !is_device_ptr(edges);
+            any_host |= h;
+            GC_TRY(stage_in(edges, sizeof(uint32_t) * 2 * m, st, ebuf, (const void**)&d_edges));
+        }
+    } else {
+        uint64_t narcs = 0;
+        bool oh = !is_device_ptr(off);
+        if (oh) {
+            narcs = off[n];
+            any_host = true;
+            GC_TRY(stage_in(off, sizeof(uint64_t) * ((size_t)n + 1), st, obuf, (const void**)&d_off));
+            if (narcs) {
+                if (is_device_ptr(cols)) {
+                    d_cols = cols;
+                } else {
+                    GC_TRY(stage_in(cols, sizeof(uint32_t) * narcs, st, cbuf, (const void**)&d_cols));
+                }
+            }
+        } else if (!is_device_ptr(cols)) {
+            GC_CUDA(cudaMemcpyAsync(&narcs, off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+            GC_CUDA(cudaStreamSynchronize(st));
+            any_host = true;
+            if (narcs) GC_TRY(stage_in(cols, sizeof(uint32_t) * narcs, st, cbuf, (const void**)&d_cols));
+        }
+    }
+    // parent array: the caller's labels buffer when it is device memory
+    uint32_t* P = nullptr;
+    bool labels_host = labels && !is_device_ptr(labels);
+    any_host |= labels_host;
+    if (labels && !labels_host) {
+        P = labels;
+    } else {
+        GC_TRY(pbuf.alloc(sizeof(uint32_t) * (size_t)n, st));
+        P = pbuf.as<uint32_t>();
+    }
+    uint32_t* H = nullptr;
+    u64w* W = nullptr;
+    uint32_t* sf = nullptr;
+    if (v.link == GCONN_LINK_HOOKS) { GC_TRY(hbuf.alloc(sizeof(uint32_t) * (size_t)n, st)); H = hbuf.as<uint32_t>(); }
+    if (v.link == GCONN_LINK_JTB) { GC_TRY(wbuf.alloc(sizeof(u64w) * (size_t)n, st)); W = wbuf.as<u64w>(); }
+    if (want_forest) { GC_TRY(sfbuf.alloc(sizeof(uint32_t) * (size_t)n, st)); sf = sfbuf.as<uint32_t>(); }
+
+    UFState s = make_state(n, P, H, W, sf, v);
+    GC_TRY(init_state(s, st));
+    if (csr && want_forest)
+        GC_TRY(launch("check_arcs", k_check_arcs, 1, 1, 0, st, d_off, n, s.err));
+
+    if (!csr) {
+        if (v.link == GCONN_LINK_SV || v.link == GCONN_LINK_LT) {
+            GC_TRY(rounds_coo(v, s, d_edges, nullptr, m, st));
+        } else {
+            GC_TRY(union_coo(v, s, d_edges, m, 0, st));
+        }
+    } else {
+        GC_TRY(csr_connect(v, s, d_off, d_cols, st));
+    }
+    if (labels) {
+        // rounds-based finishes leave P fully compressed and min-rooted
+        GC_TRY(finalize_labels(v, s, P, st));
+        if (labels_host) GC_CUDA(cudaMemcpyAsync(labels, P, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    }
+    if (want_forest) {
+        GC_TRY(sf_output(n, sf, forest, forest_count, st));
+        any_host |= !is_device_ptr(forest) || !is_device_ptr(forest_count);
+    }
+    if (any_host) return read_and_clear_err(st);
+    return GCONN_OK;
+}
+
+}  // namespace gc
+
+using namespace gc;
+
+extern "C" gconn_status gconn_cc(uint32_t n, uint64_t m, const uint32_t* edges, uint32_t* labels,
+                                 const gconn_variant* v, void* stream) {
+    return static_run(n, m, edges, nullptr, nullptr, labels, nullptr, nullptr, v, 0, stream);
+}
+
+extern "C" gconn_status gconn_cc_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols, uint32_t* labels,
+                                     const gconn_variant* v, void* stream) {
+    if (!offsets) return GCONN_E_INVAL;
+    return static_run(n, 0, nullptr, offsets, cols, labels, nullptr, nullptr, v, 0, stream);
+}
+
+extern "C" gconn_status gconn_spanning_forest(uint32_t n, uint64_t m, const uint32_t* edges, uint64_t* forest,
+                                              uint64_t* forest_count, uint32_t* labels, const gconn_variant* v,
+                                              void* stream) {
+    return static_run(n, m, edges, nullptr, nullptr, labels, forest, forest_count, v, 1, stream);
+}
+
+extern "C" gconn_status gconn_spanning_forest_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
+                                                  uint64_t* forest, uint64_t* forest_count, uint32_t* labels,
+                                                  const gconn_variant* v, void* stream) {
+    if (!offsets) return GCONN_E_INVAL;
+    return static_run(n, 0, nullptr, offsets, cols, labels, forest, forest_count, v, 1, stream);
+}

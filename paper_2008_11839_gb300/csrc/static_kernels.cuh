@@ -1,0 +1,362 @@
+// static_kernels.cuh -- kernels of the static two-phase method (Algorithm 1,
+// Algorithm 2) shared by the COO and CSR paths: label initialisation, COO
+// finish, k-out / HB sampling, full compression, L_max, vertex gathering,
+// load-balanced CSR finish, finalisation and forest compaction.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "uf_device.cuh"
+
+namespace gc {
+
+constexpr int SMALL_DEG = 32;     // CSR finish: thread per vertex up to this degree
+constexpr int TASK_ARCS = 256;    // CSR finish: arcs per warp task above it
+constexpr int LMAX_SAMPLES = 1024;
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t hash_u32(uint64_t seed, uint64_t i) {
+    unsigned long long z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return (uint32_t)((z ^ (z >> 31)) >> 32);
+}
+
+__device__ __forceinline__ bool err_abort(const uint32_t* err) {
+    return (__ldcg(err) & GC_DERR_NONCONV) != 0;
+}
+
+// InitLabel (Algorithm 1) and InitEdge (Algorithm 2): P[v] = v, hooks and
+// forest slots to "none", JTB words to (rank 0, parent v).
+static __global__ void k_init(uint32_t n, uint32_t* P, uint32_t* H, u64w* W, uint32_t* sf) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (P) P[v] = (uint32_t)v;
+        if (H) H[v] = GC_DINF;
+        if (W) W[v] = wmake(0, (uint32_t)v);
+        if (sf) sf[v] = GC_DINF;
+    }
+}
+
+// Finish phase over a COO edge list (Section 3.5 batches use it too): one
+// union per edge, grid-stride, edges streamed once.  eid_base offsets the
+// recorded forest ids (incremental batches).
+template <int L, int F, int S, bool SF>
+static __global__ void __launch_bounds__(256) k_union_coo(const uint2* __restrict__ E, uint64_t m, UFState s,
+                                                   uint32_t eid_base) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t it = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        if ((++it & 63u) == 0 && err_abort(s.err)) return;
+        uint2 e = __ldcs(E + i);
+        if (e.x >= s.n || e.y >= s.n) {
+            atomicOr(s.err, GC_DERR_RANGE);
+            continue;
+        }
+        if (e.x == e.y) continue;
+        Spin sp(s.cap);
+        uf_union<L, F, S, SF>(s, e.x, e.y, eid_base + (uint32_t)i, sp);
+    }
+}
+
+// k-out sampling (Algorithm 2, first k edges of every vertex).  One thread
+// per vertex unions its k edges serially; the k column entries of a row are
+// contiguous, so they share one or two sectors.
+template <int L, int F, int S, bool SF>
+static __global__ void __launch_bounds__(256) k_kout(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols,
+                                              int k, UFState s) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
+        uint64_t lo = off[v], hi = off[v + 1];
+        uint64_t end = lo + (uint64_t)k < hi ? lo + (uint64_t)k : hi;
+        for (uint64_t a = lo; a < end; ++a) {
+            uint32_t w = cols[a];
+            if (w >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
+            if (w == (uint32_t)v) continue;
+            Spin sp(s.cap);
+            uf_union<L, F, S, SF>(s, (uint32_t)v, w, (uint32_t)a, sp);
+        }
+    }
+}
+
+// HB sampling step 1 (Algorithm 3): P[v] = min(v, w) for the smallest
+// neighbour w = cols[off[v]].  Each thread writes only its own P[v].
+static __global__ void k_hb1(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols, uint32_t n,
+                      uint32_t* P, uint32_t* sf, uint32_t* err) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint64_t lo = off[v];
+        if (off[v + 1] > lo) {
+            uint32_t w = cols[lo];
+            if (w >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
+            if (w < (uint32_t)v) {
+                P[v] = w;
+                if (sf) sf[v] = (uint32_t)lo;
+            }
+        }
+    }
+}
+
+// HB sampling step 2: every vertex that is still a root unions its first N
+// edges.
+template <int L, int F, int S, bool SF>
+static __global__ void __launch_bounds__(256) k_hb2(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols,
+                                             int N, UFState s) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
+        uint32_t p = (L == LK_JTB) ? wpar(ldw(s.W, (uint32_t)v)) : ldp(s.P, (uint32_t)v);
+        if (p != (uint32_t)v) continue;
+        uint64_t lo = off[v], hi = off[v + 1];
+        uint64_t end = lo + (uint64_t)N < hi ? lo + (uint64_t)N : hi;
+        for (uint64_t a = lo; a < end; ++a) {
+            uint32_t w = cols[a];
+            if (w >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
+            if (w == (uint32_t)v) continue;
+            Spin sp(s.cap);
+            uf_union<L, F, S, SF>(s, (uint32_t)v, w, (uint32_t)a, sp);
+        }
+    }
+}
+
+// Full compression (the FullShortcut fixpoint): every vertex points straight
+// at its root.  Roots do not move during this kernel, so one walk per vertex
+// reaches the fixpoint of repeated pointer jumping.
+template <int L>
+static __global__ void k_compress(UFState s) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
+        uint32_t r = uf_root<L>(s, (uint32_t)v);
+        if (L == LK_JTB) {
+            u64w w = ldw(s.W, (uint32_t)v);
+            if (wpar(w) != r) s.W[v] = wmake(wrank(w), r);
+        } else {
+            if (ldp(s.P, (uint32_t)v) != r) stp(s.P, (uint32_t)v, r);
+        }
+    }
+}
+
+// Union-JTB after a min-linking step (HB step 1, BFS): the trees are flat
+// (parent = root), so roots get rank 1 and everything else rank 0, which keeps
+// every parent's key above its children's.
+static __global__ void k_w_from_p(uint32_t n, const uint32_t* P, u64w* W) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint32_t p = P[v];
+        W[v] = wmake(p == (uint32_t)v ? 1u : 0u, p);
+    }
+}
+
+// GetMostFrequentLabel (Algorithm 1): mode of the (compressed) labels of
+// LMAX_SAMPLES seeded random vertices, ties to the smaller label.  One block.
+template <int L>
+static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_t seed, uint32_t* lmax_out) {
+    __shared__ uint32_t a[LMAX_SAMPLES];
+    __shared__ unsigned long long best;
+    unsigned t = threadIdx.x;
+    if (t == 0) best = 0;
+    uint32_t x = (uint32_t)(((uint64_t)hash_u32(seed, t) * s.n) >> 32);
+    a[t] = (L == LK_JTB) ? wpar(ldw(s.W, x)) : ldp(s.P, x);
+    __syncthreads();
+    for (unsigned k = 2; k <= LMAX_SAMPLES; k <<= 1) {       // bitonic sort
+        for (unsigned j = k >> 1; j > 0; j >>= 1) {
+            unsigned p = t ^ j;
+            if (p > t) {
+                uint32_t x0 = a[t], x1 = a[p];
+                bool up = (t & k) == 0;
+                if ((x0 > x1) == up) { a[t] = x1; a[p] = x0; }
+            }
+            __syncthreads();
+        }
+    }
+    uint32_t lab = a[t];
+    if (t == 0 || a[t - 1] != lab) {                          // run start
+        unsigned lo = t, hi = LMAX_SAMPLES;                   // first index with a[] > lab
+        while (lo < hi) {
+            unsigned mid = (lo + hi) >> 1;
+            if (a[mid] > lab) hi = mid; else lo = mid + 1;
+        }
+        unsigned len = lo - t;
+        // larger count wins; on a tie the smaller label (larger ~lab) wins
+        unsigned long long key = ((unsigned long long)len << 32) | (uint32_t)(~lab);
+        atomicMax(&best, key);
+    }
+    __syncthreads();
+    if (t == 0) *lmax_out = ~(uint32_t)best;
+}
+
+// Vertex gathering (the VG optimisation): vertices whose sampled label is not
+// L_max and that have edges become active.  Low-degree ones go to a list
+// (thread per vertex); higher-degree ones are cut into TASK_ARCS-arc warp
+// tasks.  A vertex whose tasks do not fit the task array goes to the overflow
+// list (one block per vertex).  With `active` non-null one bit per vertex
+// records the active set for the arc filter of the finish kernels.
+template <int L>
+static __global__ void __launch_bounds__(256) k_vg(const uint64_t* __restrict__ off, UFState s, const uint32_t* lmax_p,
+                                            uint32_t* active, uint32_t* small, uint32_t* nsmall,
+                                            unsigned long long* tasks, uint32_t task_cap, uint32_t* ntasks,
+                                            uint32_t* over, uint32_t* nover) {
+    uint32_t lmax = lmax_p ? *lmax_p : GC_DINF;
+    uint64_t nwords = ((uint64_t)s.n + 31) / 32;
+    uint64_t wstride = (uint64_t)gridDim.x * (blockDim.x / 32);
+    unsigned lane = lane_id();
+    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nwords; w += wstride) {
+        uint64_t v = w * 32 + lane;
+        bool act = false;
+        uint64_t deg = 0;
+        if (v < s.n) {
+            deg = off[v + 1] - off[v];
+            uint32_t lab = (L == LK_JTB) ? wpar(ldw(s.W, (uint32_t)v)) : ldp(s.P, (uint32_t)v);
+            act = deg > 0 && lab != lmax;
+        }
+        unsigned am = __ballot_sync(0xFFFFFFFFu, act);
+        if (active && lane == 0) active[w] = am;
+        bool is_small = act && deg <= (uint64_t)SMALL_DEG;
+        unsigned sm = __ballot_sync(0xFFFFFFFFu, is_small);
+        if (sm) {
+            unsigned leader = __ffs(sm) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(nsmall, (uint32_t)__popc(sm));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            if (is_small) small[base + __popc(sm & ((1u << lane) - 1))] = (uint32_t)v;
+        }
+        if (act && !is_small) {
+            uint64_t nch = (deg + TASK_ARCS - 1) / TASK_ARCS;
+            uint32_t base = atomicAdd(ntasks, (uint32_t)nch);
+            if ((uint64_t)base + nch <= task_cap) {
+                for (uint64_t j = 0; j < nch; ++j) tasks[base + j] = ((unsigned long long)v << 32) | j;
+            } else {
+                over[atomicAdd(nover, 1u)] = (uint32_t)v;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ bool arc_needed(const uint32_t* active, uint32_t u, uint32_t v) {
+    // each undirected edge is processed once: from its larger endpoint when
+    // both are active, from the active one when the other was skipped
+    if (v < u) return true;
+    if (!active) return false;
+    return ((__ldg(active + (v >> 5)) >> (v & 31)) & 1u) == 0;
+}
+
+template <int L, int F, int S, bool SF>
+static __global__ void __launch_bounds__(256) k_finish_small(const uint64_t* __restrict__ off,
+                                                      const uint32_t* __restrict__ cols, UFState s,
+                                                      const uint32_t* active, const uint32_t* small,
+                                                      const uint32_t* nsmall) {
+    uint32_t cnt = *nsmall;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t it = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
+        if ((++it & 63u) == 0 && err_abort(s.err)) return;
+        uint32_t u = small[i];
+        uint64_t lo = off[u], hi = off[u + 1];
+        for (uint64_t a = lo; a < hi; ++a) {
+            uint32_t v = cols[a];
+            if (v >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
+            if (!arc_needed(active, u, v)) continue;
+            Spin sp(s.cap);
+            uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
+        }
+    }
+}
+
+template <int L, int F, int S, bool SF>
+static __global__ void __launch_bounds__(256) k_finish_tasks(const uint64_t* __restrict__ off,
+                                                      const uint32_t* __restrict__ cols, UFState s,
+                                                      const uint32_t* active, const unsigned long long* tasks,
+                                                      const uint32_t* ntasks, uint32_t task_cap) {
+    uint32_t cnt = *ntasks;
+    if (cnt > task_cap) cnt = task_cap;
+    uint64_t nw = (uint64_t)gridDim.x * (blockDim.x / 32);
+    unsigned lane = lane_id();
+    for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; t < cnt; t += nw) {
+        if (err_abort(s.err)) return;
+        unsigned long long task = tasks[t];
+        uint32_t u = (uint32_t)(task >> 32);
+        uint64_t lo = off[u] + (task & 0xFFFFFFFFull) * TASK_ARCS, hi = off[u + 1];
+        if (lo + TASK_ARCS < hi) hi = lo + TASK_ARCS;
+        for (uint64_t a = lo + lane; a < hi; a += 32) {
+            uint32_t v = cols[a];
+            if (v >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
+            if (!arc_needed(active, u, v)) continue;
+            Spin sp(s.cap);
+            uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
+        }
+    }
+}
+
+// Overflow vertices: one block strides over all arcs of one vertex.
+template <int L, int F, int S, bool SF>
+static __global__ void __launch_bounds__(256) k_finish_over(const uint64_t* __restrict__ off,
+                                                     const uint32_t* __restrict__ cols, UFState s,
+                                                     const uint32_t* active, const uint32_t* over,
+                                                     const uint32_t* nover) {
+    uint32_t cnt = *nover;
+    for (uint32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+        uint32_t u = over[i];
+        for (uint64_t a = off[u] + threadIdx.x; a < off[u + 1]; a += blockDim.x) {
+            uint32_t v = cols[a];
+            if (v >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
+            if (!arc_needed(active, u, v)) continue;
+            Spin sp(s.cap);
+            uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
+        }
+    }
+}
+
+// LabelFinalization (Algorithm 1): labels[v] = root(v).  With min-linking the
+// root is the smallest id of its tree, i.e. already canonical.
+static __global__ void k_finalize(UFState s, uint32_t* labels) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride)
+        labels[v] = uf_root<LK_ASYNC>(s, (uint32_t)v);
+}
+
+// Union-JTB roots are not minimal: canonicalise through the root.
+static __global__ void k_fill(uint32_t n, uint32_t* a, uint32_t val) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) a[v] = val;
+}
+
+static __global__ void k_jtb_min(UFState s, uint32_t* labels) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride)
+        atomicMin(labels + wpar(ldw(s.W, (uint32_t)v)), (uint32_t)v);
+}
+
+static __global__ void k_jtb_gather(UFState s, uint32_t* labels) {
+    // W is flat here; a root's own slot already holds its component minimum
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
+        uint32_t r = wpar(ldw(s.W, (uint32_t)v));
+        if (r != (uint32_t)v) labels[v] = __ldcg(labels + r);
+    }
+}
+
+// Spanning forest output: compact the recorded slots into a dense id list.
+static __global__ void k_sf_compact(uint32_t n, const uint32_t* sf, unsigned long long* out, unsigned long long* count) {
+    uint64_t nwords = ((uint64_t)n + 31) / 32;
+    uint64_t wstride = (uint64_t)gridDim.x * (blockDim.x / 32);
+    unsigned lane = lane_id();
+    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nwords; w += wstride) {
+        uint64_t v = w * 32 + lane;
+        uint32_t id = v < n ? sf[v] : GC_DINF;
+        bool has = id != GC_DINF;
+        unsigned m = __ballot_sync(0xFFFFFFFFu, has);
+        if (!m) continue;
+        unsigned leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (has) out[base + __popc(m & ((1u << lane) - 1))] = id;
+    }
+}
+
+// offsets[n] must fit a 32-bit forest id.
+static __global__ void k_check_arcs(const uint64_t* off, uint32_t n, uint32_t* err) {
+    if (off[n] >= 0xFFFFFFFFull) atomicOr(err, GC_DERR_OVERFLOW);
+}
+
+}  // namespace gc

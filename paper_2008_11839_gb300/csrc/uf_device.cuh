@@ -1,0 +1,341 @@
+// uf_device.cuh -- concurrent union-find rules on a uint32 parent array P.
+//
+// Section 2 fixes the invariant every rule here keeps: a vertex points to
+// itself (a root) or to a vertex with a smaller id, so parent chains strictly
+// decrease and can never close a cycle.  All rules are root-based: only a
+// root is ever re-pointed into another tree (by one CAS), while compression
+// only moves a non-root pointer to one of its ancestors.
+//
+// Memory model: P lives in global memory and is shared by all threads.
+// Plain loads go through L2 only (ld.global.cg), so a retry loop always sees
+// other threads' CAS results; CAS is atomicCAS (performed at L2).  Every loop
+// is bounded by Spin: after `cap` steps the operation gives up and raises
+// ERR_NONCONV in the device error word, and every other operation gives up
+// soon after seeing that flag.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gc {
+
+enum { LK_ASYNC = 0, LK_HOOKS = 1, LK_EARLY = 2, LK_REMCAS = 3, LK_JTB = 4 };
+enum { FD_NAIVE = 0, FD_COMPRESS = 1, FD_SPLIT = 2, FD_HALVE = 3, FD_TWOTRY = 4 };
+enum { SP_NONE = 0, SP_SPLIT_ONE = 1, SP_HALVE_ONE = 2, SP_SPLICE = 3 };
+
+#define GC_DINF 0xFFFFFFFFu
+#define GC_DERR_RANGE 1u
+#define GC_DERR_NONCONV 2u
+#define GC_DERR_OVERFLOW 4u
+
+typedef unsigned long long u64w;
+
+struct UFState {
+    uint32_t* P;      // parents (all min-linking rules)
+    uint32_t* H;      // hooks, INF-initialised (Union-Hooks)
+    u64w* W;          // (rank << 32) | parent words (Union-JTB)
+    uint32_t* sf;     // spanning-forest slot per vertex (edge / arc id), INF = none
+    uint32_t* err;    // device error word
+    uint32_t n;
+    uint32_t cap;     // per-operation loop cap
+    uint32_t seed;    // Union-JTB priority seed
+};
+
+__device__ __forceinline__ uint32_t ldp(const uint32_t* P, uint32_t i) { return __ldcg(P + i); }
+__device__ __forceinline__ void stp(uint32_t* P, uint32_t i, uint32_t v) { __stcg(P + i, v); }
+__device__ __forceinline__ u64w ldw(const u64w* W, uint32_t i) { return __ldcg(W + i); }
+__device__ __forceinline__ uint32_t wpar(u64w w) { return (uint32_t)w; }
+__device__ __forceinline__ uint32_t wrank(u64w w) { return (uint32_t)(w >> 32); }
+__device__ __forceinline__ u64w wmake(uint32_t rank, uint32_t par) { return ((u64w)rank << 32) | par; }
+
+struct Spin {
+    uint32_t left;
+    bool dead;
+    __device__ __forceinline__ explicit Spin(uint32_t cap) : left(cap), dead(false) {}
+    // One loop step; false once the operation must give up.
+    __device__ __forceinline__ bool step(const UFState& s) {
+        if (dead) return false;
+        if (--left == 0) {
+            atomicOr(s.err, GC_DERR_NONCONV);
+            dead = true;
+            return false;
+        }
+        if ((left & 4095u) == 0 && (__ldcg(s.err) & GC_DERR_NONCONV)) {
+            dead = true;
+            return false;
+        }
+        return true;
+    }
+};
+
+// ------------------------------------------------------------ find rules
+// Algorithm 5.  Each returns the root reached (or, after giving up, the last
+// vertex visited with sp.dead set).
+
+template <int F>
+__device__ __forceinline__ uint32_t uf_find(const UFState& s, uint32_t u, Spin& sp) {
+    uint32_t* P = s.P;
+    if (F == FD_NAIVE) {
+        uint32_t v = u;
+        while (true) {
+            uint32_t p = ldp(P, v);
+            if (p == v) return v;
+            v = p;
+            if (!sp.step(s)) return v;
+        }
+    } else if (F == FD_COMPRESS) {
+        uint32_t r = u, p = ldp(P, r);
+        if (p == r) return r;
+        while (p != r) {
+            r = p;
+            p = ldp(P, r);
+            if (!sp.step(s)) return r;
+        }
+        // every vertex on the path whose parent is above the root points at it
+        uint32_t x = u;
+        while (true) {
+            uint32_t j = ldp(P, x);
+            if (!(j > r)) break;
+            stp(P, x, r);
+            x = j;
+            if (!sp.step(s)) break;
+        }
+        return r;
+    } else if (F == FD_SPLIT) {
+        while (true) {
+            uint32_t v = ldp(P, u), w = ldp(P, v);
+            if (v == w) return v;
+            atomicCAS(P + u, v, w);
+            u = v;
+            if (!sp.step(s)) return u;
+        }
+    } else {  // FD_HALVE
+        while (true) {
+            uint32_t v = ldp(P, u), w = ldp(P, v);
+            if (v == w) return v;
+            uint32_t old = atomicCAS(P + u, v, w);
+            u = (old == v) ? w : old;  // the value P[u] holds right after the CAS
+            if (!sp.step(s)) return u;
+        }
+    }
+}
+
+// ----------------------------------------------------------- union rules
+// Each returns true iff this call re-pointed a root, and then records the
+// edge id in that root's spanning-forest slot (Section 3.2).
+
+// Union-Async (Algorithm 7).  The CAS target is P[p_u]: only a root is
+// linked, from the larger root id to the smaller.  Retries re-run the find
+// from the previous roots, which are ancestors of the endpoints.
+template <int F, bool SF>
+__device__ __forceinline__ bool union_async(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
+    uint32_t pu = uf_find<F>(s, u, sp), pv = uf_find<F>(s, v, sp);
+    while (pu != pv && !sp.dead) {
+        if (pu < pv) { uint32_t t = pu; pu = pv; pv = t; }
+        if (ldp(s.P, pu) == pu) {
+            if (atomicCAS(s.P + pu, pu, pv) == pu) {
+                if (SF) s.sf[pu] = eid;
+                return true;
+            }
+        }
+        if (!sp.step(s)) break;
+        pu = uf_find<F>(s, pu, sp);
+        pv = uf_find<F>(s, pv, sp);
+    }
+    return false;
+}
+
+// Union-Hooks (Algorithm 8): the CAS claims H[p_u]; the winner then writes
+// P[p_u] with an uncontended store followed by a memory fence.
+template <int F, bool SF>
+__device__ __forceinline__ bool union_hooks(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
+    uint32_t pu = uf_find<F>(s, u, sp), pv = uf_find<F>(s, v, sp);
+    while (pu != pv && !sp.dead) {
+        if (pu < pv) { uint32_t t = pu; pu = pv; pv = t; }
+        if (ldp(s.P, pu) == pu && atomicCAS(s.H + pu, GC_DINF, pv) == GC_DINF) {
+            stp(s.P, pu, pv);
+            __threadfence();
+            if (SF) s.sf[pu] = eid;
+            return true;
+        }
+        if (!sp.step(s)) break;
+        pu = uf_find<F>(s, pu, sp);
+        pv = uf_find<F>(s, pv, sp);
+    }
+    return false;
+}
+
+// Union-Early (Algorithm 9): climb both paths together with a halving step
+// and hook the larger side as soon as it is a root.  Hooking a root p_u under
+// any p_v < p_u is safe: every member of p_u's tree has an id >= p_u.
+template <int F, bool SF>
+__device__ __forceinline__ bool union_early(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
+    uint32_t pu = u, pv = v;
+    bool linked = false;
+    while (pu != pv) {
+        if (pu < pv) { uint32_t t = pu; pu = pv; pv = t; }
+        uint32_t z = ldp(s.P, pu);
+        if (z == pu) {
+            uint32_t old = atomicCAS(s.P + pu, pu, pv);
+            if (old == pu) {
+                if (SF) s.sf[pu] = eid;
+                linked = true;
+                break;
+            }
+            z = old;
+        }
+        uint32_t w = ldp(s.P, z);
+        if (w != z) atomicCAS(s.P + pu, z, w);
+        pu = w;
+        if (!sp.step(s)) break;
+    }
+    if (F != FD_NAIVE && !sp.dead) {
+        uf_find<F>(s, u, sp);
+        uf_find<F>(s, v, sp);
+    }
+    return linked;
+}
+
+// Splice step of Rem's algorithm (Algorithm 6), applied to the current r_u.
+template <int S>
+__device__ __forceinline__ uint32_t rem_splice(const UFState& s, uint32_t ru, uint32_t rv) {
+    uint32_t* P = s.P;
+    if (S == SP_SPLICE) {
+        uint32_t p = ldp(P, ru);
+        atomicCAS(P + ru, p, ldp(P, rv));
+        return p;
+    } else {
+        uint32_t v = ldp(P, ru), w = ldp(P, v);
+        if (v != w) atomicCAS(P + ru, v, w);
+        return S == SP_SPLIT_ONE ? v : w;
+    }
+}
+
+// Union-Rem-CAS (Algorithm 11): compare parents, link r_u onto P[r_v] when
+// r_u is a root, else splice and continue from the returned vertex.
+template <int F, int S, bool SF>
+__device__ __forceinline__ bool union_remcas(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
+    uint32_t ru = u, rv = v;
+    while (true) {
+        uint32_t pu = ldp(s.P, ru), pv = ldp(s.P, rv);
+        if (pu == pv) return false;
+        if (pu < pv) {
+            uint32_t t = ru; ru = rv; rv = t;
+            t = pu; pu = pv; pv = t;
+        }
+        if (ru == pu && atomicCAS(s.P + ru, ru, pv) == ru) {
+            if (SF) s.sf[ru] = eid;
+            if (F != FD_NAIVE) {
+                uf_find<F>(s, u, sp);
+                uf_find<F>(s, v, sp);
+            }
+            return true;
+        }
+        ru = rem_splice<S>(s, ru, rv);
+        if (!sp.step(s)) return false;
+    }
+}
+
+// ----------------------------------------------------------- Union-JTB
+// Randomized linking by rank on 64-bit (rank, parent) words: the root with
+// the smaller key (rank, priority, id) is linked under the other; on equal
+// ranks the new parent's rank is raised by a second CAS.  Keys strictly
+// increase along every parent pointer, so no cycle can form.
+
+__device__ __forceinline__ uint32_t jtb_priority(uint32_t seed, uint32_t v) {
+    unsigned long long z = (unsigned long long)seed * 0x9E3779B97F4A7C15ull + v + 1;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return (uint32_t)((z ^ (z >> 31)) >> 32);
+}
+
+template <int F>
+__device__ __forceinline__ uint32_t jtb_find(const UFState& s, uint32_t u, Spin& sp) {
+    u64w* W = s.W;
+    if (F != FD_TWOTRY) {  // FindSimple
+        while (true) {
+            uint32_t p = wpar(ldw(W, u));
+            if (p == u) return u;
+            u = p;
+            if (!sp.step(s)) return u;
+        }
+    }
+    while (true) {  // FindTwoTrySplit: up to two split attempts per step
+        u64w wu = ldw(W, u);
+        uint32_t v = wpar(wu);
+        if (v == u) return u;
+        uint32_t w = wpar(ldw(W, v));
+        if (w == v) return v;
+        for (int t = 0; t < 2; ++t) {
+            u64w old = atomicCAS(W + u, wu, wmake(wrank(wu), w));
+            if (old == wu) break;
+            wu = old;
+            v = wpar(wu);
+            w = wpar(ldw(W, v));
+            if (w == v) break;
+        }
+        u = v;
+        if (!sp.step(s)) return u;
+    }
+}
+
+template <int F, bool SF>
+__device__ __forceinline__ bool union_jtb(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
+    uint32_t ru = jtb_find<F>(s, u, sp), rv = jtb_find<F>(s, v, sp);
+    while (ru != rv && !sp.dead) {
+        u64w wu = ldw(s.W, ru), wv = ldw(s.W, rv);
+        if (wpar(wu) != ru || wpar(wv) != rv) {
+            if (!sp.step(s)) break;
+            ru = jtb_find<F>(s, ru, sp);
+            rv = jtb_find<F>(s, rv, sp);
+            continue;
+        }
+        uint32_t ku = wrank(wu), kv = wrank(wv);
+        bool u_low;
+        if (ku != kv) {
+            u_low = ku < kv;
+        } else {
+            uint32_t qu = jtb_priority(s.seed, ru), qv = jtb_priority(s.seed, rv);
+            u_low = (qu != qv) ? (qu < qv) : (ru < rv);
+        }
+        if (!u_low) {
+            uint32_t t = ru; ru = rv; rv = t;
+            u64w tw = wu; wu = wv; wv = tw;
+            t = ku; ku = kv; kv = t;
+        }
+        if (atomicCAS(s.W + ru, wu, wmake(ku, rv)) == wu) {
+            if (ku == kv) atomicCAS(s.W + rv, wv, wmake(kv + 1, rv));
+            if (SF) s.sf[ru] = eid;
+            return true;
+        }
+        if (!sp.step(s)) break;
+        ru = jtb_find<F>(s, ru, sp);
+        rv = jtb_find<F>(s, rv, sp);
+    }
+    return false;
+}
+
+// ----------------------------------------------------------- dispatcher
+template <int L, int F, int S, bool SF>
+__device__ __forceinline__ bool uf_union(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
+    if (L == LK_ASYNC) return union_async<F, SF>(s, u, v, eid, sp);
+    if (L == LK_HOOKS) return union_hooks<F, SF>(s, u, v, eid, sp);
+    if (L == LK_EARLY) return union_early<F, SF>(s, u, v, eid, sp);
+    if (L == LK_REMCAS) return union_remcas<F, S, SF>(s, u, v, eid, sp);
+    return union_jtb<F, SF>(s, u, v, eid, sp);
+}
+
+// Root of v with no compression (parent array or JTB words).  A chain has
+// at most n vertices; a longer walk means a corrupted forest and raises
+// ERR_NONCONV instead of looping.
+template <int L>
+__device__ __forceinline__ uint32_t uf_root(const UFState& s, uint32_t v) {
+    for (uint32_t i = 0; i <= s.n; ++i) {
+        uint32_t p = (L == LK_JTB) ? wpar(ldw(s.W, v)) : ldp(s.P, v);
+        if (p == v) return v;
+        v = p;
+    }
+    atomicOr(s.err, GC_DERR_NONCONV);
+    return v;
+}
+
+}  // namespace gc

@@ -1,0 +1,108 @@
+"""GPU parity of incremental connectivity (Section 3.5, Algorithm 3): a
+replay of the same insert/query stream by the sequential oracle gives the
+same answers bit for bit, and the final labels equal static components of
+everything inserted."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+import paper_2008_11839_gb300 as g
+from conftest import read_inc_golden
+from gpu_util import LT_ROOT, UF_COMBOS, combo_id, dev, host_u32
+
+pytestmark = pytest.mark.gpu
+
+INC_VARIANTS = [dict(link=l, find=f, splice=s) for (l, f, s) in UF_COMBOS] + \
+    [dict(link="sv")] + [dict(link="lt", lt=r) for r in LT_ROOT]
+
+
+def _vid(kw):
+    return "-".join(str(x) for x in kw.values())
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    g.build()
+
+
+def _stream(n, seed, nbatches=8):
+    rng = np.random.default_rng(seed)
+    scale = int(np.ceil(np.log2(n)))
+    perm = graphgen.permutation(1 << scale, seed, 6)
+    start, qstart = 0, 0
+    ops = []
+    for _ in range(nbatches):
+        b = int(rng.integers(0, 3000))
+        e = graphgen.rmat_range(scale, start, b, seed, perm=perm)
+        e = e % np.uint32(n)
+        start += b
+        q = int(rng.integers(1, 4000))
+        p = graphgen.pairs_range(n, qstart, q, seed)
+        qstart += q
+        ops.append((e, p))
+    return ops
+
+
+@pytest.mark.parametrize("kw", INC_VARIANTS, ids=_vid)
+def test_replay_matches_oracle(kw):
+    n = 6000
+    inc = g.Incremental(n, g.make_variant(**kw))
+    ref = oracle.Incremental(n)
+    allins = []
+    for e, p in _stream(n, 11):
+        inc.insert(dev(e))
+        ref.insert(e)
+        allins.append(e)
+        got = inc.query(dev(p)).cpu().numpy()
+        g.gconn_sync()
+        assert (got == ref.query(p)).all()
+    lab = host_u32(inc.labels())
+    g.gconn_sync()
+    assert (lab == oracle.cc_uf(n, np.concatenate(allins))).all()
+    inc.close()
+
+
+def test_golden_stream():
+    n, ops, labels = read_inc_golden("inc_stream.txt")
+    for kw in (dict(link="async"), dict(link="remcas", splice="splice"), dict(link="jtb")):
+        inc = g.Incremental(n, g.make_variant(**kw))
+        for op in ops:
+            if op[0] == "insert":
+                inc.insert(dev(np.array([[op[1], op[2]]], np.uint32)))
+            else:
+                got = int(inc.query(dev(np.array([[op[1], op[2]]], np.uint32))).cpu()[0])
+                assert got == op[3], (kw, op)
+        assert host_u32(inc.labels()).tolist() == labels
+        inc.close()
+
+
+def test_host_buffers_and_empty_batches():
+    n = 1000
+    h = g.gconn_inc_create(n, g.make_variant(link="async"))
+    e = graphgen.er(n, 700, 3)
+    g.gconn_inc_insert_batch(h, 0, None)
+    g.gconn_inc_insert_batch(h, len(e), e)
+    p = graphgen.pairs_range(n, 0, 500, 3)
+    out = np.empty(500, np.uint8)
+    g.gconn_inc_query(h, 500, p, out)
+    ref = oracle.cc_uf(n, e)
+    assert (out == (ref[p[:, 0]] == ref[p[:, 1]])).all()
+    lab = np.empty(n, np.uint32)
+    g.gconn_inc_labels(h, lab)
+    assert (lab == ref).all()
+    with pytest.raises(g.GconnError) as ex:
+        g.gconn_inc_query(h, 1, np.array([[0, n]], np.uint32), np.empty(1, np.uint8))
+    assert ex.value.status == g.GCONN_E_RANGE
+    g.gconn_inc_destroy(h)
+
+
+def test_incremental_rejects_non_root_based():
+    with pytest.raises(g.GconnError) as ex:
+        g.gconn_inc_create(10, g.make_variant(link="lt", lt="PUS"))
+    assert ex.value.status == g.GCONN_E_UNSUPPORTED
+    with pytest.raises(g.GconnError):
+        g.gconn_inc_create(10, g.make_variant(sample="kout"))

@@ -1,0 +1,196 @@
+"""GPU parity of static connectivity and spanning forests (Algorithms 1, 2)
+against the CPU oracle, bit-exact on canonical labels, through the C ABI."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+import paper_2008_11839_gb300 as g
+from gpu_util import LT_ALL, LT_ROOT, UF_COMBOS, combo_id, dev, host_u32, small_graphs
+
+pytestmark = pytest.mark.gpu
+
+GRAPHS = small_graphs()
+REF = {name: oracle.cc_uf(n, e) for name, n, e in GRAPHS}
+CSR = {name: graphgen.csr(n, e) for name, n, e in GRAPHS}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    g.build()
+    g.lib()
+
+
+def _cc_coo(n, e, v):
+    lab = g.cc(n, dev(e), v)
+    g.gconn_sync()
+    return host_u32(lab)
+
+
+def _cc_csr(n, off, cols, v):
+    lab = g.cc_csr(n, dev(off), dev(cols), v)
+    g.gconn_sync()
+    return host_u32(lab)
+
+
+@pytest.mark.parametrize("combo", UF_COMBOS, ids=combo_id)
+def test_coo_union_find(combo):
+    link, f, sp = combo
+    v = g.make_variant(link=link, find=f, splice=sp)
+    for name, n, e in GRAPHS:
+        assert (_cc_coo(n, e, v) == REF[name]).all(), name
+
+
+@pytest.mark.parametrize("combo", UF_COMBOS, ids=combo_id)
+def test_coo_spanning_forest(combo):
+    link, f, sp = combo
+    v = g.make_variant(link=link, find=f, splice=sp)
+    for name, n, e in GRAPHS:
+        ids, lab = g.spanning_forest(n, dev(e), v, labels=True)
+        g.gconn_sync()
+        ids = ids.cpu().numpy().astype(np.uint64)
+        assert oracle.sf_check(n, e, ids, REF[name]) == 0, name
+        assert (host_u32(lab) == REF[name]).all(), name
+
+
+@pytest.mark.parametrize("sample", ["none", "kout", "hb", "bfs"])
+@pytest.mark.parametrize("combo", UF_COMBOS, ids=combo_id)
+def test_csr_sampling_union_find(sample, combo):
+    link, f, sp = combo
+    v = g.make_variant(sample=sample, link=link, find=f, splice=sp)
+    for name, n, e in GRAPHS:
+        off, cols = CSR[name]
+        assert (_cc_csr(n, off, cols, v) == REF[name]).all(), name
+
+
+@pytest.mark.parametrize("sample", ["none", "kout", "hb", "bfs"])
+@pytest.mark.parametrize("combo", UF_COMBOS, ids=combo_id)
+def test_csr_spanning_forest(sample, combo):
+    link, f, sp = combo
+    v = g.make_variant(sample=sample, link=link, find=f, splice=sp)
+    for name, n, e in GRAPHS:
+        off, cols = CSR[name]
+        ids, lab = g.spanning_forest_csr(n, dev(off), dev(cols), v, labels=True)
+        g.gconn_sync()
+        assert oracle.sf_check_arcs(n, off, cols, ids.cpu().numpy().astype(np.uint64), REF[name]) == 0, name
+        assert (host_u32(lab) == REF[name]).all(), name
+
+
+@pytest.mark.parametrize("sample", ["none", "kout"])
+def test_shiloach_vishkin(sample):
+    v = g.make_variant(sample=sample, link="sv")
+    for name, n, e in GRAPHS:
+        if sample == "none":
+            assert (_cc_coo(n, e, v) == REF[name]).all(), name
+            ids, _ = g.spanning_forest(n, dev(e), v)
+            g.gconn_sync()
+            assert oracle.sf_check(n, e, ids.cpu().numpy().astype(np.uint64), REF[name]) == 0, name
+        off, cols = CSR[name]
+        assert (_cc_csr(n, off, cols, v) == REF[name]).all(), name
+
+
+@pytest.mark.parametrize("rules", LT_ALL)
+def test_liu_tarjan(rules):
+    for sample in ["none", "hb"]:
+        v = g.make_variant(sample=sample, link="lt", lt=rules)
+        for name, n, e in GRAPHS:
+            if sample == "none":
+                assert (_cc_coo(n, e, v) == REF[name]).all(), (name, rules)
+            off, cols = CSR[name]
+            assert (_cc_csr(n, off, cols, v) == REF[name]).all(), (name, rules, sample)
+
+
+@pytest.mark.parametrize("rules", LT_ROOT)
+def test_liu_tarjan_forest(rules):
+    v = g.make_variant(link="lt", lt=rules)
+    for name, n, e in GRAPHS:
+        ids, _ = g.spanning_forest(n, dev(e), v)
+        g.gconn_sync()
+        assert oracle.sf_check(n, e, ids.cpu().numpy().astype(np.uint64), REF[name]) == 0, (name, rules)
+        off, cols = CSR[name]
+        ids, _ = g.spanning_forest_csr(n, dev(off), dev(cols), g.make_variant(sample="kout", link="lt", lt=rules))
+        g.gconn_sync()
+        assert oracle.sf_check_arcs(n, off, cols, ids.cpu().numpy().astype(np.uint64), REF[name]) == 0
+
+
+def test_host_pointers_match():
+    """Host (numpy) inputs and outputs go through the same kernels."""
+    name, n, e = GRAPHS[0]
+    lab = np.empty(n, np.uint32)
+    g.gconn_cc(n, len(e), e, lab, g.make_variant(link="remcas", splice="splice"))
+    assert (lab == REF[name]).all()
+    off, cols = CSR[name]
+    lab2 = np.empty(n, np.uint32)
+    g.gconn_cc_csr(n, off, cols, lab2, g.make_variant(sample="kout"))
+    assert (lab2 == REF[name]).all()
+    forest = np.empty(n, np.uint64)
+    cnt = np.zeros(1, np.uint64)
+    g.gconn_spanning_forest(n, len(e), e, forest, cnt, None, None)
+    assert oracle.sf_check(n, e, forest[: int(cnt[0])], REF[name]) == 0
+
+
+def test_repeated_runs_stay_valid():
+    """Concurrent forests differ between runs; every one must be valid."""
+    name, n, e = GRAPHS[2]
+    de = dev(e)
+    for _ in range(20):
+        ids, _ = g.spanning_forest(n, de, g.make_variant(link="async"))
+        g.gconn_sync()
+        assert oracle.sf_check(n, e, ids.cpu().numpy().astype(np.uint64), REF[name]) == 0
+
+
+# ------------------------------------------------------------------ errors
+
+def test_endpoint_out_of_range_reported():
+    import torch
+    e = np.array([[0, 1], [2, 9]], np.uint32)
+    lab = torch.empty(5, dtype=torch.int32, device="cuda")
+    g.gconn_cc(5, 2, dev(e), lab)
+    with pytest.raises(g.GconnError) as ex:
+        g.gconn_sync()
+    assert ex.value.status == g.GCONN_E_RANGE
+    g.gconn_sync()                      # flag cleared
+    with pytest.raises(g.GconnError) as ex:
+        g.gconn_cc(5, 2, e, np.empty(5, np.uint32))   # host call returns it directly
+    assert ex.value.status == g.GCONN_E_RANGE
+
+
+def test_invalid_arguments():
+    import torch
+    lab = torch.empty(5, dtype=torch.int32, device="cuda")
+    with pytest.raises(g.GconnError) as ex:
+        g.gconn_cc(5, 3, None, lab)
+    assert ex.value.status == g.GCONN_E_INVAL
+    with pytest.raises(g.GconnError) as ex:
+        g.gconn_cc(5, 1, dev(np.array([[0, 1]], np.uint32)), lab, g.make_variant(sample="kout"))
+    assert ex.value.status == g.GCONN_E_UNSUPPORTED
+    with pytest.raises(g.GconnError) as ex:
+        g.gconn_cc(0xFFFFFFFF, 0, None, lab)
+    assert ex.value.status == g.GCONN_E_INVAL
+
+
+def test_iteration_cap_reports_nonconverged():
+    """A cap of one loop step on a contended star (every edge competes for
+    the centre, the largest id) must stop with E_NONCONVERGED, not hang."""
+    import torch
+    n = 20001
+    star = np.stack([np.full(n - 1, n - 1), np.arange(n - 1)], 1).astype(np.uint32)
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    g.gconn_cc(n, n - 1, dev(star), lab, g.make_variant(link="async", iter_cap=1))
+    with pytest.raises(g.GconnError) as ex:
+        g.gconn_sync()
+    assert ex.value.status == g.GCONN_E_NONCONVERGED
+    # the context stays usable
+    assert (_cc_coo(n, star, g.make_variant()) == oracle.cc_uf(n, star)).all()
+
+
+def test_empty_and_zero_vertex_inputs():
+    import torch
+    lab = torch.empty(0, dtype=torch.int32, device="cuda")
+    g.gconn_cc(0, 0, None, lab)
+    g.gconn_sync()
+    with pytest.raises(g.GconnError):
+        g.gconn_cc(0, 1, dev(np.array([[0, 0]], np.uint32)), lab)
