@@ -1,0 +1,428 @@
+"""Benchmark: static connected components on an RMAT scale-22 graph, plus the
+incremental insert/query stream, through libgconn on GB300.
+
+One step = one full static CC pass of the two-phase method (sampling, L_max,
+vertex gathering, finish, finalisation) over the resident CSR of an RMAT
+graph with 2^22 vertices and 2^26 undirected edges (Graph500 a,b,c,d =
+.57,.19,.19,.05, ids randomly permuted, self-loops and duplicates kept).
+edges/s counts the 2^26 undirected input edges per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torchrun) every rank runs its own replica
+graph (seed + rank): the static problem does not shard without an exchange
+step, so scaling is weak and there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen  # noqa: E402
+
+SCALE = 22
+M_EDGES = 1 << 26
+SEED_STATIC = 0x6C0A0002          # per-config seed: base 0x6C0A0001 + config index
+SEED_INC = 0x6C0A0005
+INC_N_SCALE = 24
+INC_TOTAL = 1 << 28
+L2_FLUSH_BYTES = 256 << 20        # > 126 MB L2
+DEFAULT_VARIANT = "kout/async/naive"
+
+
+def parse_variant(g, spec: str):
+    parts = spec.split("/")
+    sample, link = parts[0], parts[1]
+    find = parts[2] if len(parts) > 2 else "naive"
+    splice = parts[3] if len(parts) > 3 else "none"
+    kw = dict(sample=sample, link=link)
+    if link == "lt":
+        kw["lt"] = find.upper()
+    else:
+        kw["find"] = find
+        kw["splice"] = splice
+    return g.make_variant(**kw)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ input build
+def make_static_input(rank: int):
+    seed = SEED_STATIC + 1000 * rank
+    e = graphgen.rmat(SCALE, M_EDGES, seed)
+    n = 1 << SCALE
+    off, cols = graphgen.csr(n, e)
+    return n, e, off, cols, seed
+
+
+def inc_batches(seed: int):
+    """Insert-batch sizes floor(10^(3+5U)) until 2^28 (last one truncated)."""
+    h = graphgen.hash_fill(seed, 11, 0, 4096)
+    sizes, tot = [], 0
+    for x in h:
+        u = (int(x) >> 11) * 2.0 ** -53
+        b = int(10 ** (3 + 5 * u))
+        b = min(b, INC_TOTAL - tot)
+        sizes.append(b)
+        tot += b
+        if tot >= INC_TOTAL:
+            break
+    return sizes
+
+
+# ------------------------------------------------------------ roofline
+def alg_bytes(name: str, st: dict):
+    """Algorithmic DRAM bytes of one launch of a kernel (what it must move at
+    least once; random-access amplification not counted)."""
+    n = st["n"]
+    if name == "kout":
+        return 8 * (n + 1) + 4 * st["kout_arcs"] + 4 * n
+    if name in ("compress", "finalize"):
+        return 8 * n
+    if name == "init":
+        return 4 * n
+    if name == "vg":
+        return 8 * (n + 1) + 4 * n
+    if name == "union_coo":
+        return 8 * st["m"] + 4 * n
+    return None
+
+
+def profile_table(g):
+    prof = g.gconn_profile_get()
+    return {k: {"launches": c, "ms": ms} for k, (c, ms) in prof.items()}
+
+
+def pct(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * p / 100.0
+    lo, hi = int(np.floor(k)), int(np.ceil(k))
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+# ------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2008_11839_gb300 as g
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    g.build()
+    g.lib()
+    dev = torch.device("cuda", local_rank)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    n, e, off, cols, seed = make_static_input(rank)
+    deg = np.diff(off).astype(np.int64)
+    st = {"n": n, "m": M_EDGES, "narcs": int(off[-1]), "kout_arcs": int(np.minimum(deg, 2).sum())}
+    d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+    d_cols = torch.from_numpy(cols.view(np.int32)).to(dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    v = parse_variant(g, args.variant)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g.gconn_cc_csr(n, d_off, d_cols, labels, v, stream)
+
+    for i in range(args.warmup):
+        flush.fill_(i)
+        step()
+    g.gconn_sync(stream)
+
+    # parity of the benchmarked configuration against the oracle's labels is
+    # covered by the tests; here a cheap invariant check guards the numbers
+    lab = labels.cpu().numpy().view(np.uint32)
+    ok = bool((lab <= np.arange(n, dtype=np.uint32)).all() and (lab[lab] == lab).all()
+              and (lab[e[:4096, 0]] == lab[e[:4096, 1]]).all())
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    g.gconn_profile_reset()
+    g.gconn_profile_enable(True)
+    launches0 = g.gconn_launch_count()
+    clocks.start()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i + 1000)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    launches = g.gconn_launch_count() - launches0
+    g.gconn_profile_enable(False)
+    g.gconn_sync(stream)
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(x) for s, x in zip(starts, ends)]
+    ms = float(np.mean(step_ms))
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    prof = profile_table(g)
+
+    # dominant kernel's roofline from the live per-kernel events
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
+    roof = None
+    if dom[0]:
+        per_launch_ms = dom[1]["ms"] / max(dom[1]["launches"], 1)
+        b = alg_bytes(dom[0], st)
+        if b is not None:
+            ach = b / (per_launch_ms * 1e-3) / 1e9
+            roof = {"kernel": dom[0], "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(ach / hbm, 4), "traffic": None, "peak_source": peak_src,
+                    "alg_bytes_per_launch": b, "avg_launch_ms": round(per_launch_ms, 5)}
+    step_share = {k: round(vv["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-9), 4) for k, vv in prof.items()}
+
+    result = {"metric": "static CC edges/s (RMAT scale 22, 2^26 undirected edges)",
+              "value": M_EDGES * world / (ms * 1e-3), "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": round(ms, 5),
+              "ms_per_step_median": round(float(np.median(step_ms)), 5),
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+              "data": "synthetic", "gpu_launches": int(launches), "labels_invariant_ok": ok,
+              "config": {"workload": "static_cc_rmat_s22", "n": n, "m_undirected": M_EDGES,
+                         "arcs_csr": st["narcs"], "rmat_abcd": [0.57, 0.19, 0.19, 0.05], "seed": seed,
+                         "variant": args.variant, "input": "CSR (u64 offsets, u32 cols), resident",
+                         "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+              "roofline": roof, "kernel_share": step_share, "clocks": clk,
+              "wall_s_timed": round(wall, 4)}
+
+    # end to end through the C ABI with pinned host buffers
+    if rank == 0 and not args.no_e2e:
+        h_off = torch.from_numpy(off.view(np.int64)).pin_memory()
+        h_cols = torch.from_numpy(cols.view(np.int32)).pin_memory()
+        h_lab = torch.empty(n, dtype=torch.int32).pin_memory()
+        for _ in range(2):
+            g.gconn_cc_csr(n, h_off, h_cols, h_lab, v, stream)
+        tt = []
+        for i in range(args.steps):
+            flush.fill_(i)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            g.gconn_cc_csr(n, h_off, h_cols, h_lab, v, stream)   # H2D + kernels + D2H + sync
+            tt.append(time.perf_counter() - t1)
+        e2e_s = float(np.mean(tt))
+        result["e2e"] = {"value": M_EDGES / e2e_s, "unit": "edges/s",
+                         "h2d_bytes_per_step": int(off.nbytes + cols.nbytes),
+                         "d2h_bytes_per_step": int(4 * n), "ms_per_step": round(e2e_s * 1e3, 4)}
+
+    if rank == 0 and not args.no_incremental:
+        result["incremental"] = run_incremental(g, torch, dev, stream, args)
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(n, e, args.cpu_seconds)
+    if dist:
+        dist.destroy_process_group()
+    return result
+
+
+def run_incremental(g, torch, dev, stream, args):
+    """The insert/query stream on n = 2^24: 2^28 RMAT scale-24 insertions in
+    batches of log-uniform size in [10^3, 10^8], each followed by a query
+    batch of the same size of uniform random pairs."""
+    n = 1 << INC_N_SCALE
+    sizes = inc_batches(SEED_INC)
+    total = sum(sizes)
+    perm = graphgen.permutation(n, SEED_INC, 6)
+    ins = torch.empty((total, 2), dtype=torch.int32, device=dev)
+    qry = torch.empty((total, 2), dtype=torch.int32, device=dev)
+    chunk = 1 << 25
+    buf = np.empty((chunk, 2), np.uint32)
+    for s in range(0, total, chunk):
+        c = min(chunk, total - s)
+        graphgen.rmat_range(INC_N_SCALE, s, c, SEED_INC, perm=perm, out=buf[:c])
+        ins[s:s + c].copy_(torch.from_numpy(buf[:c].view(np.int32)))
+        graphgen.pairs_range(n, s, c, SEED_INC, out=buf[:c])
+        qry[s:s + c].copy_(torch.from_numpy(buf[:c].view(np.int32)))
+    out = torch.empty(total, dtype=torch.uint8, device=dev)
+    v = g.make_variant(link=args.inc_link)
+    res = {}
+    for rep in range(2):                       # first pass warms up
+        inc = g.Incremental(n, v, stream)
+        evs = []
+        s = 0
+        torch.cuda.synchronize()
+        for b in sizes:
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            inc.insert(ins[s:s + b], stream)
+            e1.record(stream)
+            inc.query(qry[s:s + b], out[s:s + b], stream)
+            e2.record(stream)
+            evs.append((b, e0, e1, e2))
+            s += b
+        torch.cuda.synchronize()
+        g.gconn_sync(stream)
+        ins_ms = [a.elapsed_time(b_) for (_, a, b_, _) in evs]
+        q_ms = [b_.elapsed_time(c) for (_, _, b_, c) in evs]
+        inc.close()
+        res = {"n": n, "inserts": total, "queries": total, "batches": len(sizes),
+               "variant": args.inc_link,
+               "updates_per_s": total / (sum(ins_ms) * 1e-3),
+               "queries_per_s": total / (sum(q_ms) * 1e-3),
+               "ops_per_s": 2 * total / ((sum(ins_ms) + sum(q_ms)) * 1e-3),
+               "insert_batch_ms_p50": round(pct(ins_ms, 50), 4), "insert_batch_ms_p99": round(pct(ins_ms, 99), 4),
+               "query_batch_ms_p50": round(pct(q_ms, 50), 4), "query_batch_ms_p99": round(pct(q_ms, 99), 4),
+               "batch_sizes_min_max": [min(sizes), max(sizes)],
+               "latency": "device time per batch, CUDA events on the launching stream",
+               "inputs": "resident in HBM"}
+    del ins, qry, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def cpu_baseline(n, e, seconds):
+    """The oracle (sequential union-find, one host core) on the first m_s
+    edges of the same edge list, m_s sized for about `seconds` of work."""
+    import oracle
+    m_s = 1 << 20
+    t0 = time.perf_counter()
+    oracle.cc_uf(n, e[:m_s])
+    dt = time.perf_counter() - t0
+    while dt < seconds / 4 and m_s < len(e):
+        m_s = min(len(e), m_s * 4)
+        t0 = time.perf_counter()
+        oracle.cc_uf(n, e[:m_s])
+        dt = time.perf_counter() - t0
+    return {"value": m_s / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {m_s} edges of the RMAT s22 COO list, all {n} vertices; O1 union-find incl. "
+                      f"min-id canonicalisation", "seconds": round(dt, 3), "host_cores_available": os.cpu_count()}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    """The oracle timed as it stands on the host cores (rank 0 only)."""
+    if rank != 0:
+        return None
+    import oracle
+    n = 1 << SCALE
+    e = graphgen.rmat(SCALE, M_EDGES, SEED_STATIC)
+    m_s = min(M_EDGES, args.ref_edges)
+    for _ in range(args.warmup):
+        oracle.cc_uf(n, e[:m_s])
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.cc_uf(n, e[:m_s])
+        ts.append(time.perf_counter() - t0)
+    val = m_s / float(np.mean(ts))
+    return {"impl": "reference", "metric": "static CC edges/s (RMAT scale 22, 2^26 undirected edges)",
+            "value": val, "unit": "edges/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(float(np.mean(ts)) * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "static_cc_rmat_s22", "n": n, "m_undirected": M_EDGES, "seed": SEED_STATIC},
+            "cpu_baseline": {"value": val, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {m_s} edges of the RMAT s22 COO list per step"},
+            "e2e": {"value": val, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default=DEFAULT_VARIANT)
+    ap.add_argument("--inc-link", default="async")
+    ap.add_argument("--no-incremental", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-edges", type=int, default=M_EDGES)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

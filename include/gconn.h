@@ -104,12 +104,15 @@ typedef struct gconn_variant {
  * CSR input and no sampling for COO input).  Returns GCONN_E_INVAL on NULL. */
 gconn_status gconn_variant_default(gconn_variant* v);
 
-/* Validate a variant for an input kind (0 = COO, 1 = CSR) and purpose
- * (want_forest = 1 for a spanning forest or an incremental handle).  Returns
+/* Validate a variant for an input kind (0 = COO, 1 = CSR) and a purpose
+ * (0 = components, 1 = spanning forest, 2 = incremental handle).  Returns
  * GCONN_OK, GCONN_E_INVAL (value out of range) or GCONN_E_UNSUPPORTED (e.g.
  * sampling on COO, COMPRESS with Rem-CAS, splice without Rem-CAS, TWOTRYSPLIT
- * without JTB, a forest with a non-root-based Liu-Tarjan rule set). */
-gconn_status gconn_variant_check(const gconn_variant* v, int input_kind, int want_forest);
+ * without JTB; for forests and incremental handles a Liu-Tarjan rule set
+ * without RootUpdate; for forests Rem-CAS with SpliceAtomic, which moves
+ * non-roots between trees and so is not root-based in the sense of
+ * Section 2). */
+gconn_status gconn_variant_check(const gconn_variant* v, int input_kind, int purpose);
 
 /* -------------------------------------------------------- static: COO */
 /* Connected components of the graph with n vertices and m undirected edges
@@ -142,7 +145,8 @@ gconn_status gconn_cc_csr(uint32_t n, const uint64_t* offsets, const uint32_t* c
  *   forest       : uint64[n] output (device or host)
  *   forest_count : uint64[1] output (device or host)
  *   labels       : optional uint32[n] canonical labels (NULL = not wanted)
- * Variant: no sampling; Liu-Tarjan only with RootUpdate rule sets. */
+ * Variant: no sampling; Liu-Tarjan only with RootUpdate rule sets; Rem-CAS
+ * only with SplitAtomicOne or HalveAtomicOne. */
 gconn_status gconn_spanning_forest(uint32_t n, uint64_t m, const uint32_t* edges,
                                    uint64_t* forest, uint64_t* forest_count, uint32_t* labels,
                                    const gconn_variant* v, void* stream);

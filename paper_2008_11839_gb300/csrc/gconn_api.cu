@@ -240,6 +240,7 @@ extern "C" gconn_status gconn_variant_default(gconn_variant* v) {
 extern "C" gconn_status gconn_variant_check(const gconn_variant* v, int input_kind, int want_forest) {
     if (!v) return GCONN_E_INVAL;
     if (input_kind != 0 && input_kind != 1) return GCONN_E_INVAL;
+    if (want_forest < 0 || want_forest > 2) return GCONN_E_INVAL;
     if (v->reserved != 0) return GCONN_E_INVAL;
     if (v->sample < 0 || v->sample > GCONN_SAMPLE_BFS) return GCONN_E_INVAL;
     if (v->link < 0 || v->link > GCONN_LINK_LT) return GCONN_E_INVAL;
@@ -252,6 +253,10 @@ extern "C" gconn_status gconn_variant_check(const gconn_variant* v, int input_ki
     if (v->splice != GCONN_SPLICE_NONE && !rem) return GCONN_E_UNSUPPORTED;
     if (v->find == GCONN_FIND_TWOTRYSPLIT && !jtb) return GCONN_E_UNSUPPORTED;
     if (rem && v->find == GCONN_FIND_COMPRESS) return GCONN_E_UNSUPPORTED;
+    // SpliceAtomic re-points non-roots into another tree: not root-based
+    // (Section 2), so it cannot record a forest; fine for incremental batches
+    if (want_forest == 1 && rem && (v->splice == GCONN_SPLICE_SPLICE || v->splice == GCONN_SPLICE_NONE))
+        return GCONN_E_UNSUPPORTED;
     if (jtb && v->find != GCONN_FIND_NAIVE && v->find != GCONN_FIND_TWOTRYSPLIT &&
         v->find != GCONN_FIND_FULLSHORTCUT)
         return GCONN_E_UNSUPPORTED;

@@ -89,7 +89,7 @@ extern "C" gconn_status gconn_inc_create(uint32_t n, const gconn_variant* vin, v
     else d.sample = GCONN_SAMPLE_NONE;
     if (d.sample != GCONN_SAMPLE_NONE) return GCONN_E_UNSUPPORTED;   // batches are COO
     Variant v;
-    GC_TRY(resolve_variant(&d, 0, 1, &v));
+    GC_TRY(resolve_variant(&d, 0, 2, &v));
     cudaStream_t st = (cudaStream_t)stream;
     gconn_inc* h = new gconn_inc();
     h->n = n;

@@ -235,7 +235,7 @@ static gconn_status static_run(uint32_t n, uint64_t m, const uint32_t* edges, co
     GC_TRY(resolve_variant(vin, csr ? 1 : 0, want_forest, &v));
     if (want_forest && (!forest || !forest_count)) return GCONN_E_INVAL;
     if (!want_forest && !labels && n) return GCONN_E_INVAL;
-    if (csr && (!off || (!cols && n))) return GCONN_E_INVAL;
+    if (csr && !off) return GCONN_E_INVAL;
     if (!csr && m && !edges) return GCONN_E_INVAL;
     if (!csr && want_forest && m >= 0xFFFFFFFFull) return GCONN_E_INVAL;
     if (!csr && m >= (1ull << 63)) return GCONN_E_INVAL;
@@ -271,6 +271,14 @@ static gconn_status static_run(uint32_t n, uint64_t m, const uint32_t* edges, co
     } else {
         uint64_t narcs = 0;
         bool oh = !is_device_ptr(off);
+        if (!cols) {   // allowed only for a graph without arcs
+            if (oh) narcs = off[n];
+            else {
+                GC_CUDA(cudaMemcpyAsync(&narcs, off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+                GC_CUDA(cudaStreamSynchronize(st));
+            }
+            if (narcs) return GCONN_E_INVAL;
+        }
         if (oh) {
             narcs = off[n];
             any_host = true;

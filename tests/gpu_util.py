@@ -18,6 +18,9 @@ LT_ALL = ["CUSA", "CRSA", "PUSA", "PRSA", "PUS", "PRS", "EUSA", "EUS",
 LT_ROOT = ["CRSA", "PRSA", "PRS", "CRFA", "PRFA", "PRF"]
 
 
+UF_FOREST = [c for c in UF_COMBOS if not (c[0] == "remcas" and c[2] == "splice")]
+
+
 def combo_id(c):
     return "-".join(c)
 

@@ -55,6 +55,7 @@ def test_forest_needs_root_based_lt(lib):
         v = g.make_variant(link="lt", lt=name)
         assert g.gconn_variant_check(v, 0, 0) == 0
         assert g.gconn_variant_check(v, 0, 1) == b.GCONN_E_UNSUPPORTED
+        assert g.gconn_variant_check(v, 0, 2) == b.GCONN_E_UNSUPPORTED
     for name in ["CRSA", "PRSA", "PRS", "CRFA", "PRFA", "PRF"]:
         assert g.gconn_variant_check(g.make_variant(link="lt", lt=name), 0, 1) == 0
     v = g.make_variant(link="lt", lt="PRF")
@@ -79,7 +80,11 @@ def test_all_valid_uf_combinations_accepted(lib):
             assert g.gconn_variant_check(g.make_variant(link=link, find=f), 0, 1) == 0
     for f in ["naive", "split", "halve"]:
         for sp in ["none", "split_one", "halve_one", "splice"]:
-            assert g.gconn_variant_check(g.make_variant(link="remcas", find=f, splice=sp), 0, 1) == 0
+            v = g.make_variant(link="remcas", find=f, splice=sp)
+            assert g.gconn_variant_check(v, 0, 0) == 0
+            assert g.gconn_variant_check(v, 0, 2) == 0           # incremental
+            want = b.GCONN_E_UNSUPPORTED if sp in ("none", "splice") else 0
+            assert g.gconn_variant_check(v, 0, 1) == want        # forest: splice is not root-based
     for f in ["naive", "twotrysplit"]:
         assert g.gconn_variant_check(g.make_variant(link="jtb", find=f), 1, 1) == 0
 

@@ -6,7 +6,7 @@ import pytest
 import graphgen
 import oracle
 import paper_2008_11839_gb300 as g
-from gpu_util import LT_ALL, LT_ROOT, UF_COMBOS, combo_id, dev, host_u32, small_graphs
+from gpu_util import LT_ALL, LT_ROOT, UF_COMBOS, UF_FOREST, combo_id, dev, host_u32, small_graphs
 
 pytestmark = pytest.mark.gpu
 
@@ -44,7 +44,7 @@ def test_coo_union_find(combo):
         assert (_cc_coo(n, e, v) == REF[name]).all(), name
 
 
-@pytest.mark.parametrize("combo", UF_COMBOS, ids=combo_id)
+@pytest.mark.parametrize("combo", UF_FOREST, ids=combo_id)
 def test_coo_spanning_forest(combo):
     link, f, sp = combo
     v = g.make_variant(link=link, find=f, splice=sp)
@@ -67,7 +67,7 @@ def test_csr_sampling_union_find(sample, combo):
 
 
 @pytest.mark.parametrize("sample", ["none", "kout", "hb", "bfs"])
-@pytest.mark.parametrize("combo", UF_COMBOS, ids=combo_id)
+@pytest.mark.parametrize("combo", UF_FOREST, ids=combo_id)
 def test_csr_spanning_forest(sample, combo):
     link, f, sp = combo
     v = g.make_variant(sample=sample, link=link, find=f, splice=sp)
@@ -114,6 +114,16 @@ def test_liu_tarjan_forest(rules):
         ids, _ = g.spanning_forest_csr(n, dev(off), dev(cols), g.make_variant(sample="kout", link="lt", lt=rules))
         g.gconn_sync()
         assert oracle.sf_check_arcs(n, off, cols, ids.cpu().numpy().astype(np.uint64), REF[name]) == 0
+
+
+def test_forest_rejects_splice():
+    import torch
+    e = dev(np.array([[0, 1]], np.uint32))
+    f = torch.empty(2, dtype=torch.int64, device="cuda")
+    c = torch.empty(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(g.GconnError) as ex:
+        g.gconn_spanning_forest(2, 1, e, f, c, None, g.make_variant(link="remcas", splice="splice"))
+    assert ex.value.status == g.GCONN_E_UNSUPPORTED
 
 
 def test_host_pointers_match():
