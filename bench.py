@@ -79,9 +79,14 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def wait_first(self, timeout=5.0):
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.02)
+
+    def stop(self, t_from=None, t_to=None):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -93,7 +98,9 @@ class ClockSampler:
             self.t.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if t_from is not None and not (t_from <= ts <= t_to):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -111,10 +118,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ input build
-def make_static_input(rank: int):
+def make_static_input(rank: int, scale: int = SCALE, m: int = M_EDGES):
     seed = SEED_STATIC + 1000 * rank
-    e = graphgen.rmat(SCALE, M_EDGES, seed)
-    n = 1 << SCALE
+    e = graphgen.rmat(scale, m, seed)
+    n = 1 << scale
     off, cols = graphgen.csr(n, e)
     return n, e, off, cols, seed
 
@@ -187,9 +194,10 @@ def run_ours(args, rank, world, local_rank):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
-    n, e, off, cols, seed = make_static_input(rank)
+    n, e, off, cols, seed = make_static_input(rank, args.scale, args.edges)
+    M = args.edges
     deg = np.diff(off).astype(np.int64)
-    st = {"n": n, "m": M_EDGES, "narcs": int(off[-1]), "kout_arcs": int(np.minimum(deg, 2).sum())}
+    st = {"n": n, "m": M, "narcs": int(off[-1]), "kout_arcs": int(np.minimum(deg, 2).sum())}
     d_off = torch.from_numpy(off.view(np.int64)).to(dev)
     d_cols = torch.from_numpy(cols.view(np.int32)).to(dev)
     labels = torch.empty(n, dtype=torch.int32, device=dev)
@@ -221,6 +229,7 @@ def run_ours(args, rank, world, local_rank):
     g.gconn_profile_enable(True)
     launches0 = g.gconn_launch_count()
     clocks.start()
+    clocks.wait_first()
     t0 = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(i + 1000)
@@ -229,9 +238,17 @@ def run_ours(args, rank, world, local_rank):
         ends[i].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    clk = clocks.stop()
     launches = g.gconn_launch_count() - launches0
     g.gconn_profile_enable(False)
+    # keep the same step loop running so the 200 ms clock samples see the load
+    t_cont = time.perf_counter()
+    while time.perf_counter() - t_cont < args.clock_window:
+        for i in range(8):
+            flush.fill_(i)
+            step()
+        torch.cuda.synchronize()
+    clk = clocks.stop(t0 - 0.05, time.perf_counter())
+    clk["window"] = f"timed region + {args.clock_window:.1f} s continuation of the same step loop"
     g.gconn_sync(stream)
     if dist:
         dist.barrier()
@@ -257,12 +274,12 @@ def run_ours(args, rank, world, local_rank):
     step_share = {k: round(vv["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-9), 4) for k, vv in prof.items()}
 
     result = {"metric": "static CC edges/s (RMAT scale 22, 2^26 undirected edges)",
-              "value": M_EDGES * world / (ms * 1e-3), "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+              "value": M * world / (ms * 1e-3), "unit": "edges/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": round(ms, 5),
               "ms_per_step_median": round(float(np.median(step_ms)), 5),
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
               "data": "synthetic", "gpu_launches": int(launches), "labels_invariant_ok": ok,
-              "config": {"workload": "static_cc_rmat_s22", "n": n, "m_undirected": M_EDGES,
+              "config": {"workload": f"static_cc_rmat_s{args.scale}", "n": n, "m_undirected": M,
                          "arcs_csr": st["narcs"], "rmat_abcd": [0.57, 0.19, 0.19, 0.05], "seed": seed,
                          "variant": args.variant, "input": "CSR (u64 offsets, u32 cols), resident",
                          "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
@@ -284,7 +301,7 @@ def run_ours(args, rank, world, local_rank):
             g.gconn_cc_csr(n, h_off, h_cols, h_lab, v, stream)   # H2D + kernels + D2H + sync
             tt.append(time.perf_counter() - t1)
         e2e_s = float(np.mean(tt))
-        result["e2e"] = {"value": M_EDGES / e2e_s, "unit": "edges/s",
+        result["e2e"] = {"value": M / e2e_s, "unit": "edges/s",
                          "h2d_bytes_per_step": int(off.nbytes + cols.nbytes),
                          "d2h_bytes_per_step": int(4 * n), "ms_per_step": round(e2e_s * 1e3, 4)}
 
@@ -397,6 +414,63 @@ def run_reference(args, rank, world):
             "e2e": {"value": val, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+SWEEP_LINKS = ([("async", f, "none") for f in ["naive", "compress", "split", "halve", "fullshortcut"]]
+               + [("hooks", f, "none") for f in ["naive", "compress", "split", "halve"]]
+               + [("early", f, "none") for f in ["naive", "compress", "split", "halve"]]
+               + [("remcas", f, s) for f in ["naive", "split", "halve"] for s in ["split_one", "halve_one", "splice"]]
+               + [("jtb", f, "none") for f in ["naive", "twotrysplit"]]
+               + [("sv", "naive", "none")]
+               + [("lt", r, "none") for r in ["PRF", "PRS", "CRFA", "PUF", "EUF", "CUFA"]])
+
+
+def run_sweep(args):
+    """Config-2 sweep: sampling x linking x compression on the RMAT s22 CSR;
+    every variant's labels are compared bit for bit with the oracle's."""
+    import torch
+    import oracle
+    import paper_2008_11839_gb300 as g
+    g.build()
+    dev = torch.device("cuda", 0)
+    n, e, off, cols, seed = make_static_input(0)
+    ref = oracle.cc_uf(n, e)
+    d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+    d_cols = torch.from_numpy(cols.view(np.int32)).to(dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    samples = args.sweep_samples.split(",")
+    rows = []
+    for sample in samples:
+        for link, f, sp in SWEEP_LINKS:
+            spec = f"{sample}/{link}/{f}/{sp}"
+            v = parse_variant(g, spec)
+            try:
+                for i in range(2):
+                    flush.fill_(i)
+                    g.gconn_cc_csr(n, d_off, d_cols, labels, v, stream)
+                g.gconn_sync(stream)
+                exact = bool((labels.cpu().numpy().view(np.uint32) == ref).all())
+                ts = []
+                for i in range(args.sweep_steps):
+                    flush.fill_(i)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    g.gconn_cc_csr(n, d_off, d_cols, labels, v, stream)
+                    b.record(stream)
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b))
+                g.gconn_sync(stream)
+                ms = float(np.median(ts))
+                row = {"variant": spec, "ms": round(ms, 4), "edges_per_s": M_EDGES / (ms * 1e-3), "exact": exact}
+            except g.GconnError as ex:
+                row = {"variant": spec, "error": str(ex)}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    ok = [r for r in rows if "ms" in r]
+    ok.sort(key=lambda r: r["ms"])
+    print(json.dumps({"sweep_best": ok[:10], "all_exact": all(r["exact"] for r in ok), "variants": len(rows)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,12 +484,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-edges", type=int, default=M_EDGES)
+    ap.add_argument("--clock-window", type=float, default=1.0)
+    ap.add_argument("--scale", type=int, default=SCALE, help="RMAT scale (default: the scale-22 workload)")
+    ap.add_argument("--edges", type=int, default=M_EDGES, help="undirected edges (default 2^26)")
+    ap.add_argument("--sweep", action="store_true", help="time every sampling x finish variant (RMAT s22)")
+    ap.add_argument("--sweep-samples", default="none,kout,hb,bfs")
+    ap.add_argument("--sweep-steps", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
