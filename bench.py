@@ -38,7 +38,7 @@ SEED_INC = 0x6C0A0005
 INC_N_SCALE = 24
 INC_TOTAL = 1 << 28
 L2_FLUSH_BYTES = 256 << 20        # > 126 MB L2
-DEFAULT_VARIANT = "kout/async/naive"
+DEFAULT_VARIANT = "kout/remcas/naive/split_one"
 
 
 def parse_variant(g, spec: str):
