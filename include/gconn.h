@@ -189,6 +189,30 @@ gconn_status gconn_inc_labels(gconn_inc* h, uint32_t* labels, void* stream);
 /* Release the handle and its device memory (synchronises its last stream). */
 gconn_status gconn_inc_destroy(gconn_inc* h);
 
+/* ------------------------------------------- components without allocation */
+/* No counterpart in the paper: this call exists for callers that must not
+ * allocate device memory -- for example when another allocator (a
+ * framework's caching pool) already owns the GPU's memory, or when a serving
+ * process runs under a fixed memory budget in which a new allocation could
+ * fail or stall the device.  It computes the same canonical labels as
+ * gconn_cc_csr, for the same inputs, without any device allocation.
+ *   n                 : at most GCONN_NOALLOC_MAX_N, else GCONN_E_INVAL
+ *   offsets, cols     : device memory only (no host staging), as gconn_cc_csr
+ *   labels            : device memory only, uint32[n] output
+ *   v                 : sampling NONE, KOUT or HB; link ASYNC, EARLY or
+ *                       REMCAS (others give GCONN_E_UNSUPPORTED)
+ * Its scratch (about 16.2 MiB) is one fixed device array inside libgconn that
+ * every GPU loading the library holds until the process exits.  All calls
+ * share that array and it keeps the previous call's contents, so calls whose
+ * GPU work overlaps (other streams, other threads) race: serialise them.  The
+ * first call on each device looks the array up (cudaGetSymbolAddress, no
+ * allocation); make that first call before any stream capture.  Like
+ * gconn_cc_csr with device buffers, it only enqueues work: device-side errors
+ * come back from gconn_sync. */
+#define GCONN_NOALLOC_MAX_N 1048576u
+gconn_status gconn_cc_csr_noalloc(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
+                                  uint32_t* labels, const gconn_variant* v, void* stream);
+
 /* ------------------------------------------------------------ utilities */
 /* Wait for `stream`, then return and clear the device error flags of the
  * current device (GCONN_E_RANGE, GCONN_E_NONCONVERGED) or GCONN_E_CUDA. */

@@ -26,6 +26,7 @@ GCONN_E_NOMEM = 3
 GCONN_E_UNSUPPORTED = 4
 GCONN_E_NONCONVERGED = 5
 GCONN_E_CUDA = 6
+GCONN_NOALLOC_MAX_N = 1 << 20
 # variant enums
 GCONN_SAMPLE_NONE, GCONN_SAMPLE_KOUT, GCONN_SAMPLE_HB, GCONN_SAMPLE_BFS = 0, 1, 2, 3
 (GCONN_LINK_ASYNC, GCONN_LINK_HOOKS, GCONN_LINK_EARLY, GCONN_LINK_REMCAS, GCONN_LINK_JTB,
@@ -89,6 +90,7 @@ _SIGS = {
     "gconn_inc_query": (_i32, [_vp, _u64, _vp, _vp, _vp]),
     "gconn_inc_labels": (_i32, [_vp, _vp, _vp]),
     "gconn_inc_destroy": (_i32, [_vp]),
+    "gconn_cc_csr_noalloc": (_i32, [_u32, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), _vp]),
     "gconn_sync": (_i32, [_vp]),
     "gconn_status_str": (ctypes.c_char_p, [_i32]),
     "gconn_launch_count": (_u64, []),
@@ -199,6 +201,12 @@ def gconn_cc(n, m, edges, labels, variant=None, stream=None):
 def gconn_cc_csr(n, offsets, cols, labels, variant=None, stream=None):
     check(lib().gconn_cc_csr(n, ptr(offsets), ptr(cols), ptr(labels), _vref(variant), stream_handle(stream)),
           "gconn_cc_csr")
+
+
+def gconn_cc_csr_noalloc(n, offsets, cols, labels, variant=None, stream=None):
+    """gconn_cc_csr without device allocation (device buffers, n <= 2^20)."""
+    check(lib().gconn_cc_csr_noalloc(n, ptr(offsets), ptr(cols), ptr(labels), _vref(variant),
+                                     stream_handle(stream)), "gconn_cc_csr_noalloc")
 
 
 def gconn_spanning_forest(n, m, edges, forest, forest_count, labels=None, variant=None, stream=None):
