@@ -35,6 +35,7 @@ SCALE = 22
 M_EDGES = 1 << 26
 SEED_STATIC = 0x6C0A0002          # per-config seed: base 0x6C0A0001 + config index
 SEED_INC = 0x6C0A0005
+SEED_BATCH = 0x6C0A0004
 INC_N_SCALE = 24
 INC_TOTAL = 1 << 28
 L2_FLUSH_BYTES = 256 << 20        # > 126 MB L2
@@ -307,6 +308,8 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0 and not args.no_incremental:
         result["incremental"] = run_incremental(g, torch, dev, stream, args)
+    if rank == 0 and not args.no_batched:
+        result["batched"] = run_batched(g, torch, dev, stream, args)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(n, e, args.cpu_seconds)
     if dist:
@@ -365,6 +368,66 @@ def run_incremental(g, torch, dev, stream, args):
                "latency": "device time per batch, CUDA events on the launching stream",
                "inputs": "resident in HBM"}
     del ins, qry, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_batched(g, torch, dev, stream, args):
+    """4,096 independent graphs (n log-uniform in [256, 65,536], average
+    degree uniform in [4, 32], half ER half RMAT) in one captured plan,
+    against one gconn_cc launch sequence per graph; both must agree exactly."""
+    G = 4096
+    vo, eo, e = graphgen.batched(G, SEED_BATCH)
+    d_vo = torch.from_numpy(vo.view(np.int64)).to(dev)
+    d_eo = torch.from_numpy(eo.view(np.int64)).to(dev)
+    d_e = torch.from_numpy(e.view(np.int32)).to(dev)
+    lab = torch.empty(int(vo[-1]), dtype=torch.int32, device=dev)
+    lab2 = torch.empty(int(vo[-1]), dtype=torch.int32, device=dev)
+    t0 = time.perf_counter()
+    tune = g.gconn_batch_autotune(G, vo, eo, d_e, lab, stream)
+    tune_s = time.perf_counter() - t0
+    h = g.gconn_batch_create(G, d_vo, d_eo, d_e, lab, tune, stream)
+    for _ in range(args.warmup):
+        g.gconn_batch_run(h, stream)
+    g.gconn_sync(stream)
+    ts = []
+    for i in range(max(args.steps, 3)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.gconn_batch_run(h, stream)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    g.gconn_sync(stream)
+    ms = float(np.mean(ts))
+    # the plain form: one gconn_cc call per graph on the same stream
+    vol, eol = vo.tolist(), eo.tolist()
+    v = g.make_variant(link="remcas", splice="split_one")
+
+    def per_graph():
+        for gi in range(G):
+            n = vol[gi + 1] - vol[gi]
+            m = eol[gi + 1] - eol[gi]
+            g.gconn_cc(n, m, d_e[eol[gi]:eol[gi + 1]], lab2[vol[gi]:vol[gi + 1]], v, stream)
+    per_graph()
+    g.gconn_sync(stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    per_graph()
+    b.record(stream)
+    b.synchronize()
+    ms_pg = a.elapsed_time(b)
+    g.gconn_sync(stream)
+    same = bool(torch.equal(lab, lab2))
+    g.gconn_batch_destroy(h)
+    m_tot = int(eo[-1])
+    res = {"graphs": G, "vertices": int(vo[-1]), "edges": m_tot, "ms": round(ms, 4),
+           "edges_per_s": m_tot / (ms * 1e-3), "graphs_per_s": G / (ms * 1e-3),
+           "per_graph_launches_ms": round(ms_pg, 3), "per_graph_edges_per_s": m_tot / (ms_pg * 1e-3),
+           "speedup_vs_per_graph": round(ms_pg / ms, 2), "identical_labels": same,
+           "tune": tune.as_dict(), "autotune_s": round(tune_s, 2),
+           "launch": "one CUDA graph replay (a persistent kernel per size class on forked streams)"}
+    del d_e, lab, lab2
     torch.cuda.empty_cache()
     return res
 
@@ -481,6 +544,7 @@ def main():
     ap.add_argument("--inc-link", default="async")
     ap.add_argument("--no-incremental", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-edges", type=int, default=M_EDGES)

@@ -189,6 +189,57 @@ gconn_status gconn_inc_labels(gconn_inc* h, uint32_t* labels, void* stream);
 /* Release the handle and its device memory (synchronises its last stream). */
 gconn_status gconn_inc_destroy(gconn_inc* h);
 
+/* ------------------------------------------------------ batched graphs */
+/* Connected components of G independent graphs in one go (no paper
+ * counterpart for the batching itself; each graph gets Algorithm 1 without
+ * sampling on COO input).  Graph g has vertices [vtx_off[g], vtx_off[g+1])
+ * and edges [edge_off[g], edge_off[g+1]) of the concatenated arrays; its
+ * edges use LOCAL ids in [0, n_g) and its labels are LOCAL min ids.
+ * Graphs with n_g <= class_max_n[last] run entirely in shared memory (16-bit
+ * parents, one CTA per graph, one persistent kernel per size class on its own
+ * stream); larger graphs use the global-memory path one launch each.
+ *   vtx_off, edge_off : uint64[G+1] (device or host; read on the host once)
+ *   edges             : uint32[2 * edge_off[G]] pairs, DEVICE memory
+ *   labels            : uint32[vtx_off[G]] output, DEVICE memory
+ * The tune table picks block size and union rule per size class; NULL = the
+ * default table, gconn_batch_autotune measures one. */
+#define GCONN_BATCH_CLASSES 4
+typedef struct gconn_batch_tune {
+    uint32_t class_max_n[GCONN_BATCH_CLASSES]; /* inclusive upper n of each class, ascending, <= 65536 */
+    int32_t block[GCONN_BATCH_CLASSES];        /* threads per CTA (multiple of 32, <= 1024) */
+    int32_t link[GCONN_BATCH_CLASSES];         /* GCONN_LINK_ASYNC or GCONN_LINK_REMCAS */
+    int32_t find[GCONN_BATCH_CLASSES];         /* GCONN_FIND_NAIVE or GCONN_FIND_HALVE (Async only) */
+} gconn_batch_tune;
+
+gconn_status gconn_batch_tune_default(gconn_batch_tune* t);
+
+/* One-shot: plan, run and wait.  Errors: E_INVAL (offsets not monotone, host
+ * edges / labels, misaligned edges, bad tune table), E_UNSUPPORTED, E_NOMEM,
+ * E_CUDA; E_RANGE (local endpoint >= n_g) via gconn_sync. */
+gconn_status gconn_cc_batched(uint32_t G, const uint64_t* vtx_off, const uint64_t* edge_off,
+                              const uint32_t* edges, uint32_t* labels, const gconn_batch_tune* tune,
+                              void* stream);
+
+/* Reusable plan bound to the given device buffers: the size classes, the
+ * largest-first order and the whole launch sequence captured once into a CUDA
+ * graph.  gconn_batch_run replays it on `stream` (asynchronous; the buffers
+ * must stay alive and may be refilled between runs); destroy frees the plan
+ * (after a device synchronisation). */
+typedef struct gconn_batch gconn_batch;
+gconn_status gconn_batch_create(uint32_t G, const uint64_t* vtx_off, const uint64_t* edge_off,
+                                const uint32_t* edges, uint32_t* labels, const gconn_batch_tune* tune,
+                                void* stream, gconn_batch** out);
+gconn_status gconn_batch_run(gconn_batch* b, void* stream);
+gconn_status gconn_batch_destroy(gconn_batch* b);
+
+/* Measure a tune table for this batch: every (block in {128,256,512,1024},
+ * rule in {Async+naive, Async+halving, Rem-CAS+SplitAtomicOne}) on each size
+ * class alone, median of three timed runs, best kept in *out.  Writes labels
+ * as a side effect.  Synchronous. */
+gconn_status gconn_batch_autotune(uint32_t G, const uint64_t* vtx_off, const uint64_t* edge_off,
+                                  const uint32_t* edges, uint32_t* labels, gconn_batch_tune* out,
+                                  void* stream);
+
 /* ------------------------------------------- components without allocation */
 /* No counterpart in the paper: this call exists for callers that must not
  * allocate device memory -- for example when another allocator (a

@@ -63,6 +63,20 @@ class gconn_variant(ctypes.Structure):
                 ("iter_cap", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+GCONN_BATCH_CLASSES = 4
+
+
+class gconn_batch_tune(ctypes.Structure):
+    _fields_ = [("class_max_n", ctypes.c_uint32 * GCONN_BATCH_CLASSES),
+                ("block", ctypes.c_int32 * GCONN_BATCH_CLASSES),
+                ("link", ctypes.c_int32 * GCONN_BATCH_CLASSES),
+                ("find", ctypes.c_int32 * GCONN_BATCH_CLASSES)]
+
+    def as_dict(self):
+        return {"class_max_n": list(self.class_max_n), "block": list(self.block),
+                "link": list(self.link), "find": list(self.find)}
+
+
 class GconnError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -91,6 +105,13 @@ _SIGS = {
     "gconn_inc_labels": (_i32, [_vp, _vp, _vp]),
     "gconn_inc_destroy": (_i32, [_vp]),
     "gconn_cc_csr_noalloc": (_i32, [_u32, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), _vp]),
+    "gconn_batch_tune_default": (_i32, [ctypes.POINTER(gconn_batch_tune)]),
+    "gconn_cc_batched": (_i32, [_u32, _vp, _vp, _vp, _vp, ctypes.POINTER(gconn_batch_tune), _vp]),
+    "gconn_batch_create": (_i32, [_u32, _vp, _vp, _vp, _vp, ctypes.POINTER(gconn_batch_tune), _vp,
+                                  ctypes.POINTER(_vp)]),
+    "gconn_batch_run": (_i32, [_vp, _vp]),
+    "gconn_batch_destroy": (_i32, [_vp]),
+    "gconn_batch_autotune": (_i32, [_u32, _vp, _vp, _vp, _vp, ctypes.POINTER(gconn_batch_tune), _vp]),
     "gconn_sync": (_i32, [_vp]),
     "gconn_status_str": (ctypes.c_char_p, [_i32]),
     "gconn_launch_count": (_u64, []),
@@ -207,6 +228,39 @@ def gconn_cc_csr_noalloc(n, offsets, cols, labels, variant=None, stream=None):
     """gconn_cc_csr without device allocation (device buffers, n <= 2^20)."""
     check(lib().gconn_cc_csr_noalloc(n, ptr(offsets), ptr(cols), ptr(labels), _vref(variant),
                                      stream_handle(stream)), "gconn_cc_csr_noalloc")
+
+
+def gconn_batch_tune_default() -> gconn_batch_tune:
+    t = gconn_batch_tune()
+    check(lib().gconn_batch_tune_default(ctypes.byref(t)), "gconn_batch_tune_default")
+    return t
+
+
+def gconn_cc_batched(G, vtx_off, edge_off, edges, labels, tune=None, stream=None):
+    check(lib().gconn_cc_batched(G, ptr(vtx_off), ptr(edge_off), ptr(edges), ptr(labels), _vref(tune),
+                                 stream_handle(stream)), "gconn_cc_batched")
+
+
+def gconn_batch_create(G, vtx_off, edge_off, edges, labels, tune=None, stream=None):
+    h = ctypes.c_void_p()
+    check(lib().gconn_batch_create(G, ptr(vtx_off), ptr(edge_off), ptr(edges), ptr(labels), _vref(tune),
+                                   stream_handle(stream), ctypes.byref(h)), "gconn_batch_create")
+    return h
+
+
+def gconn_batch_run(h, stream=None):
+    check(lib().gconn_batch_run(h, stream_handle(stream)), "gconn_batch_run")
+
+
+def gconn_batch_destroy(h):
+    check(lib().gconn_batch_destroy(h), "gconn_batch_destroy")
+
+
+def gconn_batch_autotune(G, vtx_off, edge_off, edges, labels, stream=None) -> gconn_batch_tune:
+    t = gconn_batch_tune()
+    check(lib().gconn_batch_autotune(G, ptr(vtx_off), ptr(edge_off), ptr(edges), ptr(labels), ctypes.byref(t),
+                                     stream_handle(stream)), "gconn_batch_autotune")
+    return t
 
 
 def gconn_spanning_forest(n, m, edges, forest, forest_count, labels=None, variant=None, stream=None):
