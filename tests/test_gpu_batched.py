@@ -33,7 +33,13 @@ def _run(vo, eo, e, tune=None):
 
 
 def test_batched_matches_oracle_all_classes():
-    vo, eo, e, ref = _batch(96, 3)            # sizes 16 .. 80,000: every class + the global path
+    vo, eo, e, _ = _batch(96, 3)              # sizes 16 .. 80,000: every class
+    big_n = 70_001                            # plus one graph above the shared-memory classes
+    big = graphgen.er(big_n, 120_000, 4)
+    vo = np.append(vo, vo[-1] + big_n).astype(np.uint64)
+    eo = np.append(eo, eo[-1] + len(big)).astype(np.uint64)
+    e = np.concatenate([e, big])
+    ref = oracle.batched_cc(vo, eo, e)
     assert np.diff(vo).max() > 65536
     assert (_run(vo, eo, e) == ref).all()
 
