@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(256) k_query(const uint2* __restrict__ Q, uint
             a = jtb_find<F>(s, e.x, sp);
             b = jtb_find<F>(s, e.y, sp);
         } else {
-            a = uf_find<F>(s, e.x, sp);
-            b = uf_find<F>(s, e.y, sp);
+            a = uf_find<F, true>(s, e.x, sp);   // no link happens during a query batch
+            b = uf_find<F, true>(s, e.y, sp);
         }
         out[i] = (a == b) ? 1 : 0;
     }

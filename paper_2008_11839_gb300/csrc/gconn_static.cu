@@ -161,7 +161,7 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off,
     } else if (v.sample == GCONN_SAMPLE_BFS) {
         return bfs_sample(v, s, off, cols, lmax_dev, st);   // also yields L_max
     }
-    GC_TRY(compress_all(v, s, st));
+    // the full compression after sampling is fused into vertex gathering
     if (jtb)
         return launch("lmax", k_lmax<LK_JTB>, 1, LMAX_SAMPLES, 0, st, s, v.seed, lmax_dev);
     return launch("lmax", k_lmax<LK_ASYNC>, 1, LMAX_SAMPLES, 0, st, s, v.seed, lmax_dev);
@@ -203,7 +203,7 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
     uint32_t* over = sc.over.as<uint32_t>();
     bool jtb = sv.link == GCONN_LINK_JTB;
     {
-        auto k = jtb ? k_vg<LK_JTB> : k_vg<LK_ASYNC>;
+        auto k = jtb ? k_vg<LK_JTB, true> : k_vg<LK_ASYNC, true>;
         GC_TRY(launch("vg", k, grid_for(k, 256, (uint64_t)n), 256, 0, st, off, s, lmax, active, small, cnt + 0,
                       tasks, (uint32_t)task_cap, cnt + 1, over, cnt + 2));
     }
@@ -213,14 +213,11 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
     uf_triple(v, &L, &F, &S);
     int B = block_of(v);
     return dispatch_uf(L, F, S, s.sf != nullptr, [&]<int l, int f, int sp, bool w>() {
-        auto k1 = k_finish_small<l, f, sp, w>;
-        GC_TRY(launch("finish_small", k1, grid_for(k1, B, n), B, 0, st, off, cols, s, active, small, cnt + 0));
-        auto k2 = k_finish_tasks<l, f, sp, w>;
-        GC_TRY(launch("finish_tasks", k2, grid_for(k2, B, (uint64_t)n * 32), B, 0, st, off, cols, s, active,
-                      tasks, cnt + 1, (uint32_t)task_cap));
-        auto k3 = k_finish_over<l, f, sp, w>;
-        return launch("finish_over", k3, grid_for(k3, B, (uint64_t)n * B), B, 0, st, off, cols, s, active, over,
-                      cnt + 2);
+        auto k = k_finish<l, f, sp, w>;
+        return launch("finish", k, grid_for(k, B, (uint64_t)n * 32), B, 0, st, off, cols, s,
+                      (const uint32_t*)active, (const uint32_t*)small, (const uint32_t*)(cnt + 0),
+                      (const unsigned long long*)tasks, (const uint32_t*)(cnt + 1), (uint32_t)task_cap,
+                      (const uint32_t*)over, (const uint32_t*)(cnt + 2));
     });
 }
 

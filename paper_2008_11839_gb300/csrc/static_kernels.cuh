@@ -126,7 +126,7 @@ template <int L>
 static __global__ void k_compress(UFState s) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
-        uint32_t r = uf_root<L>(s, (uint32_t)v);
+        uint32_t r = uf_root<L, true>(s, (uint32_t)v);
         if (L == LK_JTB) {
             u64w w = ldw(s.W, (uint32_t)v);
             if (wpar(w) != r) s.W[v] = wmake(wrank(w), r);
@@ -147,39 +147,40 @@ static __global__ void k_w_from_p(uint32_t n, const uint32_t* P, u64w* W) {
     }
 }
 
-// GetMostFrequentLabel (Algorithm 1): mode of the (compressed) labels of
-// LMAX_SAMPLES seeded random vertices, ties to the smaller label.  One block.
+// GetMostFrequentLabel (Algorithm 1): mode of the root labels of
+// LMAX_SAMPLES seeded random vertices, ties to the smaller label.  One block:
+// each thread walks its sample to the root and counts it in a shared-memory
+// open-addressing table; the best (count, smallest label) wins.
 template <int L>
 static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_t seed, uint32_t* lmax_out) {
-    __shared__ uint32_t a[LMAX_SAMPLES];
+    constexpr uint32_t SLOTS = 2 * LMAX_SAMPLES;
+    __shared__ uint32_t key[SLOTS];
+    __shared__ uint32_t cnt[SLOTS];
     __shared__ unsigned long long best;
     unsigned t = threadIdx.x;
-    if (t == 0) best = 0;
-    uint32_t x = (uint32_t)(((uint64_t)hash_u32(seed, t) * s.n) >> 32);
-    a[t] = (L == LK_JTB) ? wpar(ldw(s.W, x)) : ldp(s.P, x);
-    __syncthreads();
-    for (unsigned k = 2; k <= LMAX_SAMPLES; k <<= 1) {       // bitonic sort
-        for (unsigned j = k >> 1; j > 0; j >>= 1) {
-            unsigned p = t ^ j;
-            if (p > t) {
-                uint32_t x0 = a[t], x1 = a[p];
-                bool up = (t & k) == 0;
-                if ((x0 > x1) == up) { a[t] = x1; a[p] = x0; }
-            }
-            __syncthreads();
-        }
+    for (unsigned i = t; i < SLOTS; i += blockDim.x) {
+        key[i] = GC_DINF;
+        cnt[i] = 0;
     }
-    uint32_t lab = a[t];
-    if (t == 0 || a[t - 1] != lab) {                          // run start
-        unsigned lo = t, hi = LMAX_SAMPLES;                   // first index with a[] > lab
-        while (lo < hi) {
-            unsigned mid = (lo + hi) >> 1;
-            if (a[mid] > lab) hi = mid; else lo = mid + 1;
+    if (t == 0) best = 0;
+    __syncthreads();
+    uint32_t x = (uint32_t)(((uint64_t)hash_u32(seed, t) * s.n) >> 32);
+    uint32_t lab = uf_root<L, true>(s, x);
+    uint32_t slot = hash_u32(0x5A17ull, lab) & (SLOTS - 1);
+    for (uint32_t probe = 0; probe < SLOTS; ++probe) {
+        uint32_t prev = atomicCAS(&key[slot], GC_DINF, lab);
+        if (prev == GC_DINF || prev == lab) {
+            atomicAdd(&cnt[slot], 1u);
+            break;
         }
-        unsigned len = lo - t;
-        // larger count wins; on a tie the smaller label (larger ~lab) wins
-        unsigned long long key = ((unsigned long long)len << 32) | (uint32_t)(~lab);
-        atomicMax(&best, key);
+        slot = (slot + 1) & (SLOTS - 1);
+    }
+    __syncthreads();
+    for (unsigned i = t; i < SLOTS; i += blockDim.x) {
+        if (cnt[i]) {
+            // larger count wins; on a tie the smaller label (larger ~label) wins
+            atomicMax(&best, ((unsigned long long)cnt[i] << 32) | (uint32_t)(~key[i]));
+        }
     }
     __syncthreads();
     if (t == 0) *lmax_out = ~(uint32_t)best;
@@ -191,7 +192,7 @@ static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_
 // tasks.  A vertex whose tasks do not fit the task array goes to the overflow
 // list (one block per vertex).  With `active` non-null one bit per vertex
 // records the active set for the arc filter of the finish kernels.
-template <int L>
+template <int L, bool COMPRESS = false>
 static __global__ void __launch_bounds__(256) k_vg(const uint64_t* __restrict__ off, UFState s, const uint32_t* lmax_p,
                                             uint32_t* active, uint32_t* small, uint32_t* nsmall,
                                             unsigned long long* tasks, uint32_t task_cap, uint32_t* ntasks,
@@ -206,7 +207,18 @@ static __global__ void __launch_bounds__(256) k_vg(const uint64_t* __restrict__ 
         uint64_t deg = 0;
         if (v < s.n) {
             deg = off[v + 1] - off[v];
-            uint32_t lab = (L == LK_JTB) ? wpar(ldw(s.W, (uint32_t)v)) : ldp(s.P, (uint32_t)v);
+            uint32_t lab;
+            if (COMPRESS) {                 // full compression fused in: P[v] = root(v)
+                lab = uf_root<L, true>(s, (uint32_t)v);
+                if (L == LK_JTB) {
+                    u64w w = ldw(s.W, (uint32_t)v);
+                    if (wpar(w) != lab) s.W[v] = wmake(wrank(w), lab);
+                } else if (ldp(s.P, (uint32_t)v) != lab) {
+                    stp(s.P, (uint32_t)v, lab);
+                }
+            } else {
+                lab = (L == LK_JTB) ? wpar(ldw(s.W, (uint32_t)v)) : ldp(s.P, (uint32_t)v);
+            }
             act = deg > 0 && lab != lmax;
         }
         unsigned am = __ballot_sync(0xFFFFFFFFu, act);
@@ -287,6 +299,62 @@ static __global__ void __launch_bounds__(256) k_finish_tasks(const uint64_t* __r
     }
 }
 
+// The whole finish phase in one launch: 256-arc warp tasks first, then the
+// low-degree list (thread per vertex), then overflow vertices (warp per
+// vertex striding over all its arcs).
+template <int L, int F, int S, bool SF>
+__global__ void __launch_bounds__(256) k_finish(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols,
+                                               UFState s, const uint32_t* active, const uint32_t* small,
+                                               const uint32_t* nsmall, const unsigned long long* tasks,
+                                               const uint32_t* ntasks, uint32_t task_cap, const uint32_t* over,
+                                               const uint32_t* nover) {
+    uint32_t ct = *ntasks;
+    if (ct > task_cap) ct = task_cap;
+    uint64_t nw = (uint64_t)gridDim.x * (blockDim.x / 32);
+    uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    unsigned lane = lane_id();
+    for (uint64_t t = gw; t < ct; t += nw) {
+        if (err_abort(s.err)) return;
+        unsigned long long task = tasks[t];
+        uint32_t u = (uint32_t)(task >> 32);
+        uint64_t lo = off[u] + (task & 0xFFFFFFFFull) * TASK_ARCS, hi = off[u + 1];
+        if (lo + TASK_ARCS < hi) hi = lo + TASK_ARCS;
+        for (uint64_t a = lo + lane; a < hi; a += 32) {
+            uint32_t v = cols[a];
+            if (v >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
+            if (!arc_needed(active, u, v)) continue;
+            Spin sp(s.cap);
+            uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
+        }
+    }
+    uint32_t cs = *nsmall;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t it = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cs; i += stride) {
+        if ((++it & 63u) == 0 && err_abort(s.err)) return;
+        uint32_t u = small[i];
+        uint64_t lo = off[u], hi = off[u + 1];
+        for (uint64_t a = lo; a < hi; ++a) {
+            uint32_t v = cols[a];
+            if (v >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
+            if (!arc_needed(active, u, v)) continue;
+            Spin sp(s.cap);
+            uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
+        }
+    }
+    uint32_t co = *nover;
+    for (uint64_t i = gw; i < co; i += nw) {
+        uint32_t u = over[i];
+        for (uint64_t a = off[u] + lane; a < off[u + 1]; a += 32) {
+            uint32_t v = cols[a];
+            if (v >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
+            if (!arc_needed(active, u, v)) continue;
+            Spin sp(s.cap);
+            uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
+        }
+    }
+}
+
 // Overflow vertices: one block strides over all arcs of one vertex.
 template <int L, int F, int S, bool SF>
 static __global__ void __launch_bounds__(256) k_finish_over(const uint64_t* __restrict__ off,
@@ -311,7 +379,7 @@ static __global__ void __launch_bounds__(256) k_finish_over(const uint64_t* __re
 static __global__ void k_finalize(UFState s, uint32_t* labels) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride)
-        labels[v] = uf_root<LK_ASYNC>(s, (uint32_t)v);
+        labels[v] = uf_root<LK_ASYNC, true>(s, (uint32_t)v);
 }
 
 // Union-JTB roots are not minimal: canonicalise through the root.

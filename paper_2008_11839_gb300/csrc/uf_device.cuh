@@ -41,6 +41,15 @@ struct UFState {
 };
 
 __device__ __forceinline__ uint32_t ldp(const uint32_t* P, uint32_t i) { return __ldcg(P + i); }
+// L1-allowed parent load.  Every P[x] only ever decreases (roots are linked to
+// smaller ids, compression moves a pointer to an ancestor, a splice only to a
+// smaller parent), so a stale value is an older, larger parent of x in the
+// same set: walks through stale values still strictly descend, and every
+// decision is validated by a CAS whose returned value (always fresh) is what
+// the loops continue from.  Rules that retry by re-loading (Union-Hooks,
+// Union-JTB) use the L2-only ldp instead.
+template <bool L1>
+__device__ __forceinline__ uint32_t ldq(const uint32_t* P, uint32_t i) { return L1 ? __ldca(P + i) : __ldcg(P + i); }
 __device__ __forceinline__ void stp(uint32_t* P, uint32_t i, uint32_t v) { __stcg(P + i, v); }
 __device__ __forceinline__ u64w ldw(const u64w* W, uint32_t i) { return __ldcg(W + i); }
 __device__ __forceinline__ uint32_t wpar(u64w w) { return (uint32_t)w; }
@@ -71,29 +80,29 @@ struct Spin {
 // Algorithm 5.  Each returns the root reached (or, after giving up, the last
 // vertex visited with sp.dead set).
 
-template <int F>
+template <int F, bool L1 = false>
 __device__ __forceinline__ uint32_t uf_find(const UFState& s, uint32_t u, Spin& sp) {
     uint32_t* P = s.P;
     if (F == FD_NAIVE) {
         uint32_t v = u;
         while (true) {
-            uint32_t p = ldp(P, v);
+            uint32_t p = ldq<L1>(P, v);
             if (p == v) return v;
             v = p;
             if (!sp.step(s)) return v;
         }
     } else if (F == FD_COMPRESS) {
-        uint32_t r = u, p = ldp(P, r);
+        uint32_t r = u, p = ldq<L1>(P, r);
         if (p == r) return r;
         while (p != r) {
             r = p;
-            p = ldp(P, r);
+            p = ldq<L1>(P, r);
             if (!sp.step(s)) return r;
         }
         // every vertex on the path whose parent is above the root points at it
         uint32_t x = u;
         while (true) {
-            uint32_t j = ldp(P, x);
+            uint32_t j = ldq<L1>(P, x);
             if (!(j > r)) break;
             stp(P, x, r);
             x = j;
@@ -102,7 +111,7 @@ __device__ __forceinline__ uint32_t uf_find(const UFState& s, uint32_t u, Spin& 
         return r;
     } else if (F == FD_SPLIT) {
         while (true) {
-            uint32_t v = ldp(P, u), w = ldp(P, v);
+            uint32_t v = ldq<L1>(P, u), w = ldq<L1>(P, v);
             if (v == w) return v;
             atomicCAS(P + u, v, w);
             u = v;
@@ -110,7 +119,7 @@ __device__ __forceinline__ uint32_t uf_find(const UFState& s, uint32_t u, Spin& 
         }
     } else {  // FD_HALVE
         while (true) {
-            uint32_t v = ldp(P, u), w = ldp(P, v);
+            uint32_t v = ldq<L1>(P, u), w = ldq<L1>(P, v);
             if (v == w) return v;
             uint32_t old = atomicCAS(P + u, v, w);
             u = (old == v) ? w : old;  // the value P[u] holds right after the CAS
@@ -128,18 +137,20 @@ __device__ __forceinline__ uint32_t uf_find(const UFState& s, uint32_t u, Spin& 
 // from the previous roots, which are ancestors of the endpoints.
 template <int F, bool SF>
 __device__ __forceinline__ bool union_async(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
-    uint32_t pu = uf_find<F>(s, u, sp), pv = uf_find<F>(s, v, sp);
+    uint32_t pu = uf_find<F, true>(s, u, sp), pv = uf_find<F, true>(s, v, sp);
     while (pu != pv && !sp.dead) {
         if (pu < pv) { uint32_t t = pu; pu = pv; pv = t; }
-        if (ldp(s.P, pu) == pu) {
-            if (atomicCAS(s.P + pu, pu, pv) == pu) {
+        uint32_t p = ldq<true>(s.P, pu);
+        if (p == pu) {
+            p = atomicCAS(s.P + pu, pu, pv);
+            if (p == pu) {
                 if (SF) s.sf[pu] = eid;
                 return true;
             }
         }
         if (!sp.step(s)) break;
-        pu = uf_find<F>(s, pu, sp);
-        pv = uf_find<F>(s, pv, sp);
+        pu = uf_find<F, true>(s, p, sp);     // p is a (possibly older) parent of pu: strictly smaller
+        pv = uf_find<F, true>(s, pv, sp);
     }
     return false;
 }
@@ -173,7 +184,7 @@ __device__ __forceinline__ bool union_early(const UFState& s, uint32_t u, uint32
     bool linked = false;
     while (pu != pv) {
         if (pu < pv) { uint32_t t = pu; pu = pv; pv = t; }
-        uint32_t z = ldp(s.P, pu);
+        uint32_t z = ldq<true>(s.P, pu);
         if (z == pu) {
             uint32_t old = atomicCAS(s.P + pu, pu, pv);
             if (old == pu) {
@@ -183,54 +194,62 @@ __device__ __forceinline__ bool union_early(const UFState& s, uint32_t u, uint32
             }
             z = old;
         }
-        uint32_t w = ldp(s.P, z);
+        uint32_t w = ldq<true>(s.P, z);
         if (w != z) atomicCAS(s.P + pu, z, w);
         pu = w;
         if (!sp.step(s)) break;
     }
     if (F != FD_NAIVE && !sp.dead) {
-        uf_find<F>(s, u, sp);
-        uf_find<F>(s, v, sp);
+        uf_find<F, true>(s, u, sp);
+        uf_find<F, true>(s, v, sp);
     }
     return linked;
 }
 
-// Splice step of Rem's algorithm (Algorithm 6), applied to the current r_u.
-template <int S>
-__device__ __forceinline__ uint32_t rem_splice(const UFState& s, uint32_t ru, uint32_t rv) {
-    uint32_t* P = s.P;
-    if (S == SP_SPLICE) {
-        uint32_t p = ldp(P, ru);
-        atomicCAS(P + ru, p, ldp(P, rv));
-        return p;
-    } else {
-        uint32_t v = ldp(P, ru), w = ldp(P, v);
-        if (v != w) atomicCAS(P + ru, v, w);
-        return S == SP_SPLIT_ONE ? v : w;
-    }
-}
-
-// Union-Rem-CAS (Algorithm 11): compare parents, link r_u onto P[r_v] when
-// r_u is a root, else splice and continue from the returned vertex.
+// Union-Rem-CAS (Algorithm 11) with the splice step of Algorithm 6 applied to
+// the current r_u.  The loop carries the parent values it has loaded instead
+// of re-reading them: P[r_u] after a step is the value the step just read (or
+// the CAS returned).  Carried values may be older than memory; every P[x]
+// only decreases and sets only merge while unions run, so "equal parents"
+// still means "same set", and a link happens only through a CAS that checks
+// r_u is still a root.
 template <int F, int S, bool SF>
 __device__ __forceinline__ bool union_remcas(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
+    uint32_t* P = s.P;
     uint32_t ru = u, rv = v;
+    uint32_t pu = ldq<true>(P, ru), pv = ldq<true>(P, rv);
     while (true) {
-        uint32_t pu = ldp(s.P, ru), pv = ldp(s.P, rv);
         if (pu == pv) return false;
         if (pu < pv) {
             uint32_t t = ru; ru = rv; rv = t;
             t = pu; pu = pv; pv = t;
         }
-        if (ru == pu && atomicCAS(s.P + ru, ru, pv) == ru) {
-            if (SF) s.sf[ru] = eid;
-            if (F != FD_NAIVE) {
-                uf_find<F>(s, u, sp);
-                uf_find<F>(s, v, sp);
+        if (ru == pu) {
+            uint32_t old = atomicCAS(P + ru, ru, pv);
+            if (old == ru) {
+                if (SF) s.sf[ru] = eid;
+                if (F != FD_NAIVE) {
+                    uf_find<F, true>(s, u, sp);
+                    uf_find<F, true>(s, v, sp);
+                }
+                return true;
             }
-            return true;
+            pu = old;                       // r_u was linked meanwhile: its fresh parent
+        } else if (S == SP_SPLICE) {        // P[r_u] <- P[r_v], continue from the old parent
+            atomicCAS(P + ru, pu, pv);
+            ru = pu;
+            pu = ldq<true>(P, ru);
+        } else {                            // one split (return the parent) or halve (grandparent)
+            uint32_t w = ldq<true>(P, pu);
+            if (w != pu) atomicCAS(P + ru, pu, w);
+            if (S == SP_SPLIT_ONE) {
+                ru = pu;
+                pu = w;
+            } else {
+                ru = w;
+                pu = ldq<true>(P, w);
+            }
         }
-        ru = rem_splice<S>(s, ru, rv);
         if (!sp.step(s)) return false;
     }
 }
@@ -327,10 +346,10 @@ __device__ __forceinline__ bool uf_union(const UFState& s, uint32_t u, uint32_t 
 // Root of v with no compression (parent array or JTB words).  A chain has
 // at most n vertices; a longer walk means a corrupted forest and raises
 // ERR_NONCONV instead of looping.
-template <int L>
+template <int L, bool L1 = false>
 __device__ __forceinline__ uint32_t uf_root(const UFState& s, uint32_t v) {
     for (uint32_t i = 0; i <= s.n; ++i) {
-        uint32_t p = (L == LK_JTB) ? wpar(ldw(s.W, v)) : ldp(s.P, v);
+        uint32_t p = (L == LK_JTB) ? wpar(ldw(s.W, v)) : ldq<L1>(s.P, v);
         if (p == v) return v;
         v = p;
     }
