@@ -189,6 +189,25 @@ gconn_status gconn_inc_labels(gconn_inc* h, uint32_t* labels, void* stream);
 /* Release the handle and its device memory (synchronises its last stream). */
 gconn_status gconn_inc_destroy(gconn_inc* h);
 
+/* ----------------------------------------------------- captured plans */
+/* No paper counterpart.  The whole static pass for one input (the same work
+ * as gconn_cc / gconn_cc_csr on the same arguments) captured once into a CUDA
+ * graph; gconn_plan_run replays it on `stream`, so a repeated computation on
+ * the same buffers (their contents may change between runs) costs one graph
+ * launch instead of one host launch per kernel.  All buffers must be device
+ * memory and stay alive while the plan exists.  Variants whose pass reads a
+ * device flag on the host every round (BFS sampling, SV, Liu-Tarjan) cannot
+ * be captured: GCONN_E_UNSUPPORTED.  Device-side errors come back from
+ * gconn_sync.  If profiling is on while a plan is created, its kernels' event
+ * pairs are captured too and each replay queues them for gconn_profile_sync. */
+typedef struct gconn_plan gconn_plan;
+gconn_status gconn_plan_create_cc(uint32_t n, uint64_t m, const uint32_t* edges, uint32_t* labels,
+                                  const gconn_variant* v, gconn_plan** out);
+gconn_status gconn_plan_create_cc_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
+                                      uint32_t* labels, const gconn_variant* v, gconn_plan** out);
+gconn_status gconn_plan_run(gconn_plan* p, void* stream);
+gconn_status gconn_plan_destroy(gconn_plan* p);
+
 /* ------------------------------------------------------ batched graphs */
 /* Connected components of G independent graphs in one go (no paper
  * counterpart for the batching itself; each graph gets Algorithm 1 without
@@ -282,6 +301,9 @@ uint64_t gconn_launch_count(void);
  * (GCONN_E_INVAL once i is past the last one). */
 gconn_status gconn_profile_enable(int on);
 gconn_status gconn_profile_reset(void);
+/* Collect every queued event pair now (waits for them).  Needed after each
+ * replay of a profiled plan, whose events re-record on every replay. */
+gconn_status gconn_profile_sync(void);
 gconn_status gconn_profile_get(int i, const char** name, uint64_t* launches, double* total_ms);
 
 #ifdef __cplusplus

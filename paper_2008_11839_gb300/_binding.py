@@ -112,6 +112,11 @@ _SIGS = {
     "gconn_batch_run": (_i32, [_vp, _vp]),
     "gconn_batch_destroy": (_i32, [_vp]),
     "gconn_batch_autotune": (_i32, [_u32, _vp, _vp, _vp, _vp, ctypes.POINTER(gconn_batch_tune), _vp]),
+    "gconn_plan_create_cc": (_i32, [_u32, _u64, _vp, _vp, ctypes.POINTER(gconn_variant), ctypes.POINTER(_vp)]),
+    "gconn_plan_create_cc_csr": (_i32, [_u32, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), ctypes.POINTER(_vp)]),
+    "gconn_plan_run": (_i32, [_vp, _vp]),
+    "gconn_plan_destroy": (_i32, [_vp]),
+    "gconn_profile_sync": (_i32, []),
     "gconn_sync": (_i32, [_vp]),
     "gconn_status_str": (ctypes.c_char_p, [_i32]),
     "gconn_launch_count": (_u64, []),
@@ -294,6 +299,32 @@ def gconn_inc_labels(h, labels, stream=None):
 
 def gconn_inc_destroy(h):
     check(lib().gconn_inc_destroy(h), "gconn_inc_destroy")
+
+
+def gconn_plan_create_cc(n, m, edges, labels, variant=None):
+    h = ctypes.c_void_p()
+    check(lib().gconn_plan_create_cc(n, m, ptr(edges), ptr(labels), _vref(variant), ctypes.byref(h)),
+          "gconn_plan_create_cc")
+    return h
+
+
+def gconn_plan_create_cc_csr(n, offsets, cols, labels, variant=None):
+    h = ctypes.c_void_p()
+    check(lib().gconn_plan_create_cc_csr(n, ptr(offsets), ptr(cols), ptr(labels), _vref(variant), ctypes.byref(h)),
+          "gconn_plan_create_cc_csr")
+    return h
+
+
+def gconn_plan_run(h, stream=None):
+    check(lib().gconn_plan_run(h, stream_handle(stream)), "gconn_plan_run")
+
+
+def gconn_plan_destroy(h):
+    check(lib().gconn_plan_destroy(h), "gconn_plan_destroy")
+
+
+def gconn_profile_sync():
+    check(lib().gconn_profile_sync(), "gconn_profile_sync")
 
 
 def gconn_sync(stream=None):

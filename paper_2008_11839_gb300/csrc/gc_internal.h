@@ -9,6 +9,7 @@
 
 #include <atomic>
 #include <utility>
+#include <vector>
 
 #include "../../include/gconn.h"
 
@@ -61,6 +62,23 @@ extern std::atomic<bool> g_profiling;
 void prof_begin(const char* name, cudaStream_t st, void** token);
 void prof_end(void* token, cudaStream_t st);
 
+// Per-kernel event pairs captured into a CUDA graph: while a capture sink is
+// set on this thread, prof_end hands its record to the sink instead of the
+// global pending list; a replay re-queues the captured records (their events
+// re-record on every replay, so each replay must be collected before the next).
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+struct ProfSink {
+    std::vector<ProfRec> recs;
+    uint64_t launches = 0;
+};
+void prof_set_sink(ProfSink* sink);
+void count_capture_launch();
+void prof_requeue(const ProfSink& sink);
+void prof_release(ProfSink& sink);
+
 // Persistent-style grid: min(ceil(work / block), resident blocks on all SMs).
 template <class K>
 unsigned grid_for(K kernel, int block, uint64_t work, size_t smem = 0) {
@@ -78,6 +96,7 @@ template <class... KArgs, class... Args>
 gconn_status launch(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                     cudaStream_t st, Args&&... args) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    count_capture_launch();
     void* tok = nullptr;
     if (g_profiling.load(std::memory_order_relaxed)) prof_begin(name, st, &tok);
     kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);

@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
@@ -119,7 +120,15 @@ gconn_status stage_in(const void* src, size_t bytes, cudaStream_t st, DevBuf& bu
 struct PendingRec {
     std::string name;
     cudaEvent_t a, b;
+    bool pooled;      // events return to the pool after collection (not graph-owned)
 };
+static thread_local ProfSink* t_sink = nullptr;
+
+void prof_set_sink(ProfSink* sink) { t_sink = sink; }
+
+void count_capture_launch() {
+    if (t_sink) t_sink->launches++;
+}
 struct Total {
     uint64_t launches = 0;
     double ms = 0;
@@ -129,6 +138,7 @@ static std::vector<PendingRec> g_pending;
 static std::vector<cudaEvent_t> g_event_pool;
 static std::vector<std::string> g_order;
 static std::map<std::string, Total> g_totals;
+static std::deque<std::string> g_sink_names;   // stable storage for captured kernel names
 
 static cudaEvent_t take_event() {
     if (!g_event_pool.empty()) {
@@ -143,7 +153,15 @@ static cudaEvent_t take_event() {
 
 void prof_begin(const char* name, cudaStream_t st, void** token) {
     std::lock_guard<std::mutex> lk(g_pmu);
-    PendingRec* r = new PendingRec{name, take_event(), take_event()};
+    PendingRec* r;
+    if (t_sink) {   // graph-owned events: created fresh, kept by the plan
+        cudaEvent_t a = nullptr, b = nullptr;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        r = new PendingRec{name, a, b, false};
+    } else {
+        r = new PendingRec{name, take_event(), take_event(), true};
+    }
     cudaEventRecord(r->a, st);
     *token = r;
 }
@@ -152,8 +170,29 @@ void prof_end(void* token, cudaStream_t st) {
     PendingRec* r = (PendingRec*)token;
     cudaEventRecord(r->b, st);
     std::lock_guard<std::mutex> lk(g_pmu);
-    g_pending.push_back(*r);
+    if (t_sink) {
+        // the name is a string literal of the launching code: safe to keep
+        t_sink->recs.push_back(ProfRec{nullptr, r->a, r->b});
+        t_sink->recs.back().name = nullptr;
+        g_sink_names.push_back(r->name);
+        t_sink->recs.back().name = g_sink_names.back().c_str();
+    } else {
+        g_pending.push_back(*r);
+    }
     delete r;
+}
+
+void prof_requeue(const ProfSink& sink) {
+    std::lock_guard<std::mutex> lk(g_pmu);
+    for (const ProfRec& r : sink.recs) g_pending.push_back(PendingRec{r.name, r.a, r.b, false});
+}
+
+void prof_release(ProfSink& sink) {
+    for (ProfRec& r : sink.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    sink.recs.clear();
 }
 
 static void prof_collect() {
@@ -166,8 +205,10 @@ static void prof_collect() {
         Total& t = g_totals[r.name];
         t.launches++;
         t.ms += ms;
-        g_event_pool.push_back(r.a);
-        g_event_pool.push_back(r.b);
+        if (r.pooled) {
+            g_event_pool.push_back(r.a);
+            g_event_pool.push_back(r.b);
+        }
     }
     g_pending.clear();
 }
@@ -297,6 +338,11 @@ extern "C" gconn_status gconn_profile_reset(void) {
     std::lock_guard<std::mutex> lk(g_pmu);
     g_totals.clear();
     g_order.clear();
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_profile_sync(void) {
+    prof_collect();
     return GCONN_OK;
 }
 

@@ -158,6 +158,7 @@ struct gconn_batch {
     cudaEvent_t fork = nullptr, join[NCLS] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    ProfSink sink;                  // kernels and profiling events captured in the graph
 };
 
 namespace gc {
@@ -233,6 +234,7 @@ static gconn_status enqueue_batch(gconn_batch* b, cudaStream_t st) {
 
 static void batch_free(gconn_batch* b) {
     if (!b) return;
+    prof_release(b->sink);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (int c = 0; c < NCLS; ++c) {
@@ -376,6 +378,7 @@ extern "C" gconn_status gconn_batch_create(uint32_t G, const uint64_t* vtx_off, 
         return GCONN_E_CUDA;
     }
     gconn_status s = GCONN_OK;
+    prof_set_sink(&b->sink);
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) s = GCONN_E_CUDA;
     if (s == GCONN_OK) {
         gconn_status e = enqueue_batch(b, cap);
@@ -385,6 +388,7 @@ extern "C" gconn_status gconn_batch_create(uint32_t G, const uint64_t* vtx_off, 
         else if (ce != cudaSuccess) s = GCONN_E_CUDA;
         b->graph = gr;
     }
+    prof_set_sink(nullptr);
     if (s == GCONN_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) s = GCONN_E_CUDA;
     cudaStreamDestroy(cap);
     if (s != GCONN_OK) {
@@ -398,8 +402,9 @@ extern "C" gconn_status gconn_batch_create(uint32_t G, const uint64_t* vtx_off, 
 
 extern "C" gconn_status gconn_batch_run(gconn_batch* b, void* stream) {
     if (!b) return GCONN_E_INVAL;
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    g_launches.fetch_add(b->sink.launches, std::memory_order_relaxed);
     GC_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    if (!b->sink.recs.empty()) prof_requeue(b->sink);
     return GCONN_OK;
 }
 

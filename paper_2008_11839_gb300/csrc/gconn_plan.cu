@@ -1,0 +1,106 @@
+// gconn_plan.cu -- static connected components captured once into a CUDA
+// graph and replayed: the whole pass of Algorithm 1 (init, sampling, L_max,
+// vertex gathering, finish, finalisation) becomes one graph launch, so the
+// device runs its kernels back to back without a host launch per kernel.
+// Only variants whose pass needs no host round trip can be captured
+// (sampling none / k-out / HB, union-find finishes).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gc_internal.h"
+
+using namespace gc;
+
+struct gconn_plan {
+    int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ProfSink sink;
+};
+
+namespace {
+
+template <class Body>
+gconn_status capture_plan(Body&& body, gconn_plan** out) {
+    if (!err_word()) return GCONN_E_CUDA;   // resolved before any capture
+    gconn_plan* p = new gconn_plan();
+    cudaGetDevice(&p->device);
+    cudaStream_t cap = nullptr;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        delete p;
+        return GCONN_E_CUDA;
+    }
+    gconn_status s = GCONN_OK;
+    prof_set_sink(&p->sink);
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        s = GCONN_E_CUDA;
+    } else {
+        gconn_status b = body(cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cap, &g);
+        p->graph = g;
+        if (b != GCONN_OK) s = b;
+        else if (e != cudaSuccess) s = GCONN_E_CUDA;
+    }
+    prof_set_sink(nullptr);
+    if (s == GCONN_OK && cudaGraphInstantiate(&p->exec, p->graph, 0) != cudaSuccess) s = GCONN_E_CUDA;
+    cudaStreamDestroy(cap);
+    if (s != GCONN_OK) {
+        cudaGetLastError();
+        gconn_plan_destroy(p);
+        return s;
+    }
+    *out = p;
+    return GCONN_OK;
+}
+
+gconn_status plan_variant_ok(const gconn_variant* vin, int input_kind) {
+    Variant v;
+    GC_TRY(resolve_variant(vin, input_kind, 0, &v));
+    if (v.sample == GCONN_SAMPLE_BFS || v.link == GCONN_LINK_SV || v.link == GCONN_LINK_LT)
+        return GCONN_E_UNSUPPORTED;   // these read a device flag on the host every round
+    return GCONN_OK;
+}
+
+}  // namespace
+
+extern "C" gconn_status gconn_plan_create_cc(uint32_t n, uint64_t m, const uint32_t* edges, uint32_t* labels,
+                                             const gconn_variant* v, gconn_plan** out) {
+    if (!out) return GCONN_E_INVAL;
+    *out = nullptr;
+    if (!labels || !is_device_ptr(labels) || (m && (!edges || !is_device_ptr(edges)))) return GCONN_E_INVAL;
+    GC_TRY(plan_variant_ok(v, 0));
+    return capture_plan([&](cudaStream_t st) { return gconn_cc(n, m, edges, labels, v, st); }, out);
+}
+
+extern "C" gconn_status gconn_plan_create_cc_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
+                                                 uint32_t* labels, const gconn_variant* v, gconn_plan** out) {
+    if (!out) return GCONN_E_INVAL;
+    *out = nullptr;
+    if (!offsets || !cols || !labels || !is_device_ptr(offsets) || !is_device_ptr(cols) || !is_device_ptr(labels))
+        return GCONN_E_INVAL;
+    GC_TRY(plan_variant_ok(v, 1));
+    return capture_plan([&](cudaStream_t st) { return gconn_cc_csr(n, offsets, cols, labels, v, st); }, out);
+}
+
+extern "C" gconn_status gconn_plan_run(gconn_plan* p, void* stream) {
+    if (!p || !p->exec) return GCONN_E_INVAL;
+    g_launches.fetch_add(p->sink.launches, std::memory_order_relaxed);
+    GC_CUDA(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+    if (!p->sink.recs.empty()) prof_requeue(p->sink);
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_plan_destroy(gconn_plan* p) {
+    if (!p) return GCONN_E_INVAL;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    prof_release(p->sink);
+    cudaSetDevice(prev);
+    delete p;
+    return GCONN_OK;
+}

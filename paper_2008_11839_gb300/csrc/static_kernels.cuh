@@ -31,7 +31,18 @@ __device__ __forceinline__ bool err_abort(const uint32_t* err) {
 // forest slots to "none", JTB words to (rank 0, parent v).
 static __global__ void k_init(uint32_t n, uint32_t* P, uint32_t* H, u64w* W, uint32_t* sf) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (P && !H && !W && !sf && ((uintptr_t)P & 15u) == 0) {   // P only: 16-byte stores
+        uint64_t nv = n / 4;
+        uint4* P4 = reinterpret_cast<uint4*>(P);
+        for (uint64_t i = t0; i < nv; i += stride) {
+            uint32_t b = (uint32_t)(4 * i);
+            P4[i] = make_uint4(b, b + 1, b + 2, b + 3);
+        }
+        for (uint64_t v = nv * 4 + t0; v < n; v += stride) P[v] = (uint32_t)v;
+        return;
+    }
+    for (uint64_t v = t0; v < n; v += stride) {
         if (P) P[v] = (uint32_t)v;
         if (H) H[v] = GC_DINF;
         if (W) W[v] = wmake(0, (uint32_t)v);
@@ -166,14 +177,19 @@ static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_
     __syncthreads();
     uint32_t x = (uint32_t)(((uint64_t)hash_u32(seed, t) * s.n) >> 32);
     uint32_t lab = uf_root<L, true>(s, x);
-    uint32_t slot = hash_u32(0x5A17ull, lab) & (SLOTS - 1);
-    for (uint32_t probe = 0; probe < SLOTS; ++probe) {
-        uint32_t prev = atomicCAS(&key[slot], GC_DINF, lab);
-        if (prev == GC_DINF || prev == lab) {
-            atomicAdd(&cnt[slot], 1u);
-            break;
+    // lanes holding the same label add it once (the big component's label
+    // would otherwise serialise hundreds of shared-memory atomics)
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, lab);
+    if ((unsigned)(__ffs(peers) - 1) == lane_id()) {
+        uint32_t slot = hash_u32(0x5A17ull, lab) & (SLOTS - 1);
+        for (uint32_t probe = 0; probe < SLOTS; ++probe) {
+            uint32_t prev = atomicCAS(&key[slot], GC_DINF, lab);
+            if (prev == GC_DINF || prev == lab) {
+                atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
+                break;
+            }
+            slot = (slot + 1) & (SLOTS - 1);
         }
-        slot = (slot + 1) & (SLOTS - 1);
     }
     __syncthreads();
     for (unsigned i = t; i < SLOTS; i += blockDim.x) {
