@@ -97,6 +97,7 @@ gconn_status launch(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 
                     cudaStream_t st, Args&&... args) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     count_capture_launch();
+    cudaGetLastError();   // report this launch's error only
     void* tok = nullptr;
     if (g_profiling.load(std::memory_order_relaxed)) prof_begin(name, st, &tok);
     kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);

@@ -162,13 +162,16 @@ void prof_begin(const char* name, cudaStream_t st, void** token) {
     } else {
         r = new PendingRec{name, take_event(), take_event(), true};
     }
-    cudaEventRecord(r->a, st);
+    // inside a capture an event becomes a graph node only as an external record
+    if (t_sink) cudaEventRecordWithFlags(r->a, st, cudaEventRecordExternal);
+    else cudaEventRecord(r->a, st);
     *token = r;
 }
 
 void prof_end(void* token, cudaStream_t st) {
     PendingRec* r = (PendingRec*)token;
-    cudaEventRecord(r->b, st);
+    if (t_sink) cudaEventRecordWithFlags(r->b, st, cudaEventRecordExternal);
+    else cudaEventRecord(r->b, st);
     std::lock_guard<std::mutex> lk(g_pmu);
     if (t_sink) {
         // the name is a string literal of the launching code: safe to keep
@@ -199,8 +202,10 @@ static void prof_collect() {
     std::lock_guard<std::mutex> lk(g_pmu);
     for (auto& r : g_pending) {
         float ms = 0;
-        cudaEventSynchronize(r.b);
-        cudaEventElapsedTime(&ms, r.a, r.b);
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();   // an unreadable pair is skipped, never left as a pending error
+            ms = 0;
+        }
         if (!g_totals.count(r.name)) g_order.push_back(r.name);
         Total& t = g_totals[r.name];
         t.launches++;
