@@ -344,7 +344,7 @@ def run_incremental(g, torch, dev, stream, args):
         graphgen.pairs_range(n, s, c, SEED_INC, out=buf[:c])
         qry[s:s + c].copy_(torch.from_numpy(buf[:c].view(np.int32)))
     out = torch.empty(total, dtype=torch.uint8, device=dev)
-    v = g.make_variant(link=args.inc_link)
+    v = parse_variant(g, "none/" + args.inc_variant)
     res = {}
     for rep in range(2):                       # first pass warms up
         inc = g.Incremental(n, v, stream)
@@ -366,7 +366,7 @@ def run_incremental(g, torch, dev, stream, args):
         q_ms = [b_.elapsed_time(c) for (_, _, b_, c) in evs]
         inc.close()
         res = {"n": n, "inserts": total, "queries": total, "batches": len(sizes),
-               "variant": args.inc_link,
+               "variant": args.inc_variant,
                "updates_per_s": total / (sum(ins_ms) * 1e-3),
                "queries_per_s": total / (sum(q_ms) * 1e-3),
                "ops_per_s": 2 * total / ((sum(ins_ms) + sum(q_ms)) * 1e-3),
@@ -549,7 +549,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default=DEFAULT_VARIANT)
-    ap.add_argument("--inc-link", default="async")
+    ap.add_argument("--inc-variant", default="async/naive", help="link/find[/splice] of the incremental handle")
     ap.add_argument("--no-incremental", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

@@ -73,21 +73,45 @@ static __global__ void __launch_bounds__(256) k_union_coo(const uint2* __restric
 
 // k-out sampling (Algorithm 2, first k edges of every vertex).  One thread
 // per vertex unions its k edges serially; the k column entries of a row are
-// contiguous, so they share one or two sectors.
+// contiguous, so they share one or two sectors.  The loop is software
+// pipelined: the next vertex's offsets and first two columns are loaded
+// before the current vertex's unions run, so their DRAM latency overlaps the
+// unions' L2 round trips.
 template <int L, int F, int S, bool SF>
 static __global__ void __launch_bounds__(256) k_kout(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols,
                                               int k, UFState s) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
-        uint64_t lo = off[v], hi = off[v + 1];
+    uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t lo = 0, hi = 0;
+    uint32_t c0 = GC_DINF, c1 = GC_DINF;
+    auto fetch = [&](uint64_t x, uint64_t& flo, uint64_t& fhi, uint32_t& f0, uint32_t& f1) {
+        flo = fhi = 0;
+        f0 = f1 = GC_DINF;
+        if (x < s.n) {
+            flo = off[x];
+            fhi = off[x + 1];
+            if (fhi > flo) f0 = cols[flo];
+            if (k > 1 && fhi > flo + 1) f1 = cols[flo + 1];
+        }
+    };
+    fetch(v, lo, hi, c0, c1);
+    while (v < s.n) {
+        uint64_t nv = v + stride, nlo, nhi;
+        uint32_t n0, n1;
+        fetch(nv, nlo, nhi, n0, n1);
         uint64_t end = lo + (uint64_t)k < hi ? lo + (uint64_t)k : hi;
         for (uint64_t a = lo; a < end; ++a) {
-            uint32_t w = cols[a];
+            uint32_t w = a == lo ? c0 : (a == lo + 1 ? c1 : cols[a]);
             if (w >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
             if (w == (uint32_t)v) continue;
             Spin sp(s.cap);
             uf_union<L, F, S, SF>(s, (uint32_t)v, w, (uint32_t)a, sp);
         }
+        v = nv;
+        lo = nlo;
+        hi = nhi;
+        c0 = n0;
+        c1 = n1;
     }
 }
 
@@ -392,10 +416,40 @@ static __global__ void __launch_bounds__(256) k_finish_over(const uint64_t* __re
 
 // LabelFinalization (Algorithm 1): labels[v] = root(v).  With min-linking the
 // root is the smallest id of its tree, i.e. already canonical.
+// Four independent walks per thread advance in lock step, so four parent
+// loads are in flight at a time.
 static __global__ void k_finalize(UFState s, uint32_t* labels) {
+    constexpr int W = 4;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride)
-        labels[v] = uf_root<LK_ASYNC, true>(s, (uint32_t)v);
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; base < s.n; base += W * stride) {
+        uint32_t cur[W], nxt[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            uint64_t x = base + (uint64_t)j * stride;
+            cur[j] = x < s.n ? (uint32_t)x : GC_DINF;
+            nxt[j] = x < s.n ? ldq<true>(s.P, (uint32_t)x) : GC_DINF;
+        }
+        for (uint32_t step = 0; step <= s.n; ++step) {
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                if (nxt[j] != cur[j]) {
+                    cur[j] = nxt[j];
+                    any = true;
+                }
+            }
+            if (!any) break;
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                if (cur[j] != GC_DINF) nxt[j] = ldq<true>(s.P, cur[j]);
+            if (step == s.n) atomicOr(s.err, GC_DERR_NONCONV);
+        }
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            uint64_t x = base + (uint64_t)j * stride;
+            if (x < s.n) labels[x] = cur[j];
+        }
+    }
 }
 
 // Union-JTB roots are not minimal: canonicalise through the root.
