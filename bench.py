@@ -549,7 +549,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default=DEFAULT_VARIANT)
-    ap.add_argument("--inc-variant", default="async/naive", help="link/find[/splice] of the incremental handle")
+    ap.add_argument("--inc-variant", default="early/naive", help="link/find[/splice] of the incremental handle")
     ap.add_argument("--no-incremental", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

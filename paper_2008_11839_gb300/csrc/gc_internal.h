@@ -114,6 +114,18 @@ struct Variant {
 };
 gconn_status resolve_variant(const gconn_variant* in, int input_kind, int want_forest, Variant* out);
 
+// Optional L2 persistence window over the parent array for the launches on
+// one stream (GCONN_L2_WINDOW=1): sets the stream's access-policy window and
+// restores the previous one on destruction.  The persisting-L2 carve-out is a
+// limit of this process's context only.
+struct L2Window {
+    cudaStream_t st = nullptr;
+    cudaStreamAttrValue old{};
+    bool set = false;
+    void apply(cudaStream_t s, void* base, size_t bytes);
+    ~L2Window();
+};
+
 // Staging of possibly-host arrays onto the device.
 gconn_status stage_in(const void* src, size_t bytes, cudaStream_t st, DevBuf& buf, const void** dev);
 

@@ -3,6 +3,7 @@
 // validation for libgconn.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <deque>
@@ -114,6 +115,49 @@ gconn_status stage_in(const void* src, size_t bytes, cudaStream_t st, DevBuf& bu
     GC_CUDA(cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, st));
     *dev = buf.p;
     return GCONN_OK;
+}
+
+// -------------------------------------------------------- L2 window
+void L2Window::apply(cudaStream_t s, void* base, size_t bytes) {
+    static int enabled = -1;
+    if (enabled < 0) {
+        const char* e = getenv("GCONN_L2_WINDOW");
+        enabled = (e && e[0] == '1') ? 1 : 0;
+    }
+    if (!enabled || !s || !base || !bytes) return;
+    int dev = 0, max_persist = 0, max_window = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+    if (max_persist <= 0 || max_window <= 0) return;
+    size_t carve = bytes < (size_t)max_persist ? bytes : (size_t)max_persist;
+    size_t cur = 0;
+    cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    if (cur < carve && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, carve) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (cudaStreamGetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &old) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaStreamAttrValue v{};
+    size_t win = bytes < (size_t)max_window ? bytes : (size_t)max_window;
+    v.accessPolicyWindow.base_ptr = base;
+    v.accessPolicyWindow.num_bytes = win;
+    v.accessPolicyWindow.hitRatio = (float)((double)carve / (double)win > 1.0 ? 1.0 : (double)carve / (double)win);
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    if (cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &v) == cudaSuccess) {
+        st = s;
+        set = true;
+    } else {
+        cudaGetLastError();
+    }
+}
+
+L2Window::~L2Window() {
+    if (set) cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &old);
 }
 
 // ------------------------------------------------------------- profiling

@@ -312,6 +312,8 @@ static gconn_status static_run(uint32_t n, uint64_t m, const uint32_t* edges, co
     if (want_forest) { GC_TRY(sfbuf.alloc(sizeof(uint32_t) * (size_t)n, st)); sf = sfbuf.as<uint32_t>(); }
 
     UFState s = make_state(n, P, H, W, sf, v);
+    L2Window l2win;
+    l2win.apply(st, P, sizeof(uint32_t) * (size_t)n);
     GC_TRY(init_state(s, st));
     if (csr && want_forest)
         GC_TRY(launch("check_arcs", k_check_arcs, 1, 1, 0, st, d_off, n, s.err));

@@ -87,11 +87,11 @@ static __global__ void __launch_bounds__(256) k_kout(const uint64_t* __restrict_
     auto fetch = [&](uint64_t x, uint64_t& flo, uint64_t& fhi, uint32_t& f0, uint32_t& f1) {
         flo = fhi = 0;
         f0 = f1 = GC_DINF;
-        if (x < s.n) {
-            flo = off[x];
-            fhi = off[x + 1];
-            if (fhi > flo) f0 = cols[flo];
-            if (k > 1 && fhi > flo + 1) f1 = cols[flo + 1];
+        if (x < s.n) {   // evict-first: the rows stream once, P should stay in L2
+            flo = __ldcs(off + x);
+            fhi = __ldcs(off + x + 1);
+            if (fhi > flo) f0 = __ldcs(cols + flo);
+            if (k > 1 && fhi > flo + 1) f1 = __ldcs(cols + flo + 1);
         }
     };
     fetch(v, lo, hi, c0, c1);
@@ -246,7 +246,7 @@ static __global__ void __launch_bounds__(256) k_vg(const uint64_t* __restrict__ 
         bool act = false;
         uint64_t deg = 0;
         if (v < s.n) {
-            deg = off[v + 1] - off[v];
+            deg = __ldcs(off + v + 1) - __ldcs(off + v);
             uint32_t lab;
             if (COMPRESS) {                 // full compression fused in: P[v] = root(v)
                 lab = uf_root<L, true>(s, (uint32_t)v);
