@@ -144,7 +144,7 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off,
     if (v.sample == GCONN_SAMPLE_KOUT) {
         GC_TRY(dispatch_uf(L, F, S, sf, [&]<int l, int f, int sp, bool w>() {
             auto k = k_kout<l, f, sp, w>;
-            return launch("kout", k, grid_for(k, B, n), B, 0, st, off, cols, v.k, s);
+            return launch("kout", k, grid_for(k, KOUT_BLOCK, n), KOUT_BLOCK, 0, st, off, cols, v.k, s);
         }));
     } else if (v.sample == GCONN_SAMPLE_HB) {
         GC_TRY(launch("hb1", k_hb1, grid_for(k_hb1, 256, n), 256, 0, st, off, cols, n, s.P, s.sf, s.err));

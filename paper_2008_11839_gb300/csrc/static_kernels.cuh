@@ -71,47 +71,67 @@ static __global__ void __launch_bounds__(256) k_union_coo(const uint2* __restric
     }
 }
 
-// k-out sampling (Algorithm 2, first k edges of every vertex).  One thread
-// per vertex unions its k edges serially; the k column entries of a row are
-// contiguous, so they share one or two sectors.  The loop is software
-// pipelined: the next vertex's offsets and first two columns are loaded
-// before the current vertex's unions run, so their DRAM latency overlaps the
-// unions' L2 round trips.
+// k-out sampling (Algorithm 2, first k edges of every vertex).  A warp takes
+// 32 consecutive vertices, reads their first k <= KOUT_WARP_K column entries
+// (one sector per row), and packs the union jobs into a per-warp list in
+// shared memory with a ballot prefix, so all 32 lanes then drain a dense list:
+// isolated vertices (often ~40 % of an RMAT graph) and short rows leave no lane
+// idle.  Larger k falls back to one thread per vertex.
+constexpr int KOUT_WARP_K = 2;
+constexpr int KOUT_BLOCK = 256;
+
+struct KoutJob {
+    uint32_t u, v, eid;
+};
+
 template <int L, int F, int S, bool SF>
-static __global__ void __launch_bounds__(256) k_kout(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols,
-                                              int k, UFState s) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint64_t lo = 0, hi = 0;
-    uint32_t c0 = GC_DINF, c1 = GC_DINF;
-    auto fetch = [&](uint64_t x, uint64_t& flo, uint64_t& fhi, uint32_t& f0, uint32_t& f1) {
-        flo = fhi = 0;
-        f0 = f1 = GC_DINF;
-        if (x < s.n) {   // evict-first: the rows stream once, P should stay in L2
-            flo = __ldcs(off + x);
-            fhi = __ldcs(off + x + 1);
-            if (fhi > flo) f0 = __ldcs(cols + flo);
-            if (k > 1 && fhi > flo + 1) f1 = __ldcs(cols + flo + 1);
+static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __restrict__ off,
+                                                            const uint32_t* __restrict__ cols, int k, UFState s) {
+    __shared__ KoutJob jobs[KOUT_BLOCK / 32][32 * KOUT_WARP_K];
+    if (k > KOUT_WARP_K) {
+        uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+        for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
+            uint64_t lo = off[v], hi = off[v + 1];
+            uint64_t end = lo + (uint64_t)k < hi ? lo + (uint64_t)k : hi;
+            for (uint64_t a = lo; a < end; ++a) {
+                uint32_t w = cols[a];
+                if (w >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
+                if (w == (uint32_t)v) continue;
+                Spin sp(s.cap);
+                uf_union<L, F, S, SF>(s, (uint32_t)v, w, (uint32_t)a, sp);
+            }
         }
-    };
-    fetch(v, lo, hi, c0, c1);
-    while (v < s.n) {
-        uint64_t nv = v + stride, nlo, nhi;
-        uint32_t n0, n1;
-        fetch(nv, nlo, nhi, n0, n1);
-        uint64_t end = lo + (uint64_t)k < hi ? lo + (uint64_t)k : hi;
-        for (uint64_t a = lo; a < end; ++a) {
-            uint32_t w = a == lo ? c0 : (a == lo + 1 ? c1 : cols[a]);
-            if (w >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
-            if (w == (uint32_t)v) continue;
+        return;
+    }
+    KoutJob* my = jobs[threadIdx.x / 32];
+    unsigned lane = lane_id();
+    unsigned lt = (1u << lane) - 1;
+    uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    uint64_t nwords = ((uint64_t)s.n + 31) / 32;
+    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nwords; w += nwarps) {
+        uint64_t v = w * 32 + lane;
+        uint32_t c0 = GC_DINF, c1 = GC_DINF;
+        uint64_t lo = 0;
+        if (v < s.n) {
+            lo = off[v];
+            uint64_t hi = off[v + 1];
+            if (hi > lo) c0 = cols[lo];
+            if (k > 1 && hi > lo + 1) c1 = cols[lo + 1];
+        }
+        if ((c0 != GC_DINF && c0 >= s.n) || (c1 != GC_DINF && c1 >= s.n)) atomicOr(s.err, GC_DERR_RANGE);
+        bool j0 = c0 < s.n && c0 != (uint32_t)v;
+        bool j1 = c1 < s.n && c1 != (uint32_t)v;
+        unsigned m0 = __ballot_sync(0xFFFFFFFFu, j0), m1 = __ballot_sync(0xFFFFFFFFu, j1);
+        unsigned n0 = __popc(m0), total = n0 + __popc(m1);
+        if (j0) my[__popc(m0 & lt)] = KoutJob{(uint32_t)v, c0, (uint32_t)lo};
+        if (j1) my[n0 + __popc(m1 & lt)] = KoutJob{(uint32_t)v, c1, (uint32_t)(lo + 1)};
+        __syncwarp();
+        for (unsigned j = lane; j < total; j += 32) {
+            KoutJob jb = my[j];
             Spin sp(s.cap);
-            uf_union<L, F, S, SF>(s, (uint32_t)v, w, (uint32_t)a, sp);
+            uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
         }
-        v = nv;
-        lo = nlo;
-        hi = nhi;
-        c0 = n0;
-        c1 = n1;
+        __syncwarp();
     }
 }
 
@@ -246,7 +266,7 @@ static __global__ void __launch_bounds__(256) k_vg(const uint64_t* __restrict__ 
         bool act = false;
         uint64_t deg = 0;
         if (v < s.n) {
-            deg = __ldcs(off + v + 1) - __ldcs(off + v);
+            deg = off[v + 1] - off[v];
             uint32_t lab;
             if (COMPRESS) {                 // full compression fused in: P[v] = root(v)
                 lab = uf_root<L, true>(s, (uint32_t)v);
@@ -367,19 +387,47 @@ __global__ void __launch_bounds__(256) k_finish(const uint64_t* __restrict__ off
             uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
         }
     }
+    // low-degree vertices, flattened per warp: 32 listed vertices' arcs form one
+    // range [0, total) that the lanes cover densely (owner lane found by a
+    // shuffle binary search over the inclusive degree scan)
     uint32_t cs = *nsmall;
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    uint32_t it = 0;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cs; i += stride) {
-        if ((++it & 63u) == 0 && err_abort(s.err)) return;
-        uint32_t u = small[i];
-        uint64_t lo = off[u], hi = off[u + 1];
-        for (uint64_t a = lo; a < hi; ++a) {
+    for (uint64_t base = gw * 32; base < cs; base += nw * 32) {
+        if (err_abort(s.err)) return;
+        uint64_t i = base + lane;
+        uint32_t u = 0, d = 0;
+        uint64_t lo = 0;
+        if (i < cs) {
+            u = small[i];
+            lo = off[u];
+            d = (uint32_t)(off[u + 1] - lo);
+        }
+        uint32_t inc = d;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if ((int)lane >= o) inc += t;
+        }
+        uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        uint32_t exc = inc - d;
+        for (uint32_t jb = 0; jb < total; jb += 32) {
+            uint32_t j = jb + lane;
+            int l0 = 0, l1 = 31;                       // first lane whose inclusive sum exceeds j
+#pragma unroll
+            for (int step = 0; step < 5; ++step) {
+                int mid = (l0 + l1) >> 1;
+                uint32_t vm = __shfl_sync(0xFFFFFFFFu, inc, mid);
+                if (vm > j) l1 = mid; else l0 = mid + 1;
+            }
+            uint32_t ou = __shfl_sync(0xFFFFFFFFu, u, l0);
+            uint64_t olo = __shfl_sync(0xFFFFFFFFu, lo, l0);
+            uint32_t oex = __shfl_sync(0xFFFFFFFFu, exc, l0);
+            if (j >= total) continue;
+            uint64_t a = olo + (j - oex);
             uint32_t v = cols[a];
             if (v >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
-            if (!arc_needed(active, u, v)) continue;
+            if (!arc_needed(active, ou, v)) continue;
             Spin sp(s.cap);
-            uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
+            uf_union<L, F, S, SF>(s, ou, v, (uint32_t)a, sp);
         }
     }
     uint32_t co = *nover;
