@@ -142,9 +142,18 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off,
     bool sf = s.sf != nullptr;
     bool jtb = v.link == GCONN_LINK_JTB;
     if (v.sample == GCONN_SAMPLE_KOUT) {
+        // deferred long unions: capacity n/8 jobs, overflow runs in place
+        DevBuf qbuf, qcnt;
+        uint32_t qcap = n / 8 + 64;
+        GC_TRY(qbuf.alloc(sizeof(KoutJob) * (size_t)qcap, st));
+        GC_TRY(qcnt.alloc(sizeof(unsigned long long), st));
+        GC_CUDA(cudaMemsetAsync(qcnt.p, 0, sizeof(unsigned long long), st));
+        JobQueue dq{qbuf.as<KoutJob>(), qcnt.as<unsigned long long>(), qcap};
         GC_TRY(dispatch_uf(L, F, S, sf, [&]<int l, int f, int sp, bool w>() {
             auto k = k_kout<l, f, sp, w>;
-            return launch("kout", k, grid_for(k, KOUT_BLOCK, n), KOUT_BLOCK, 0, st, off, cols, v.k, s);
+            GC_TRY(launch("kout", k, grid_for(k, KOUT_BLOCK, n), KOUT_BLOCK, 0, st, off, cols, v.k, s, dq));
+            auto kj = k_union_jobs<l, f, sp, w>;
+            return launch("kout_deferred", kj, grid_for(kj, 256, qcap), 256, 0, st, s, dq);
         }));
     } else if (v.sample == GCONN_SAMPLE_HB) {
         GC_TRY(launch("hb1", k_hb1, grid_for(k_hb1, 256, n), 256, 0, st, off, cols, n, s.P, s.sf, s.err));

@@ -84,9 +84,22 @@ struct KoutJob {
     uint32_t u, v, eid;
 };
 
+// Deferred unions: a union that has not finished within KOUT_FAST_STEPS loop
+// steps is abandoned (the forest it leaves is valid: only root links and
+// compression happened) and re-run later from its endpoints by
+// k_union_jobs, so a few long climbs do not hold 31 idle lanes.
+constexpr uint32_t KOUT_FAST_STEPS = 8;
+
+struct JobQueue {
+    KoutJob* jobs;
+    unsigned long long* count;
+    uint32_t cap;
+};
+
 template <int L, int F, int S, bool SF>
 static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __restrict__ off,
-                                                            const uint32_t* __restrict__ cols, int k, UFState s) {
+                                                            const uint32_t* __restrict__ cols, int k, UFState s,
+                                                            JobQueue dq) {
     __shared__ KoutJob jobs[KOUT_BLOCK / 32][32 * KOUT_WARP_K];
     if (k > KOUT_WARP_K) {
         uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -128,10 +141,33 @@ static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __re
         __syncwarp();
         for (unsigned j = lane; j < total; j += 32) {
             KoutJob jb = my[j];
+            if (dq.jobs) {
+                Spin fast(KOUT_FAST_STEPS, true);
+                uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, fast);
+                if (!fast.dead) continue;
+                unsigned long long slot = atomicAdd(dq.count, 1ull);
+                if (slot < dq.cap) {
+                    dq.jobs[slot] = jb;
+                    continue;
+                }
+            }
             Spin sp(s.cap);
             uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
         }
         __syncwarp();
+    }
+}
+
+// Unions deferred by k_kout, re-run from their endpoints with the full cap.
+template <int L, int F, int S, bool SF>
+static __global__ void __launch_bounds__(256) k_union_jobs(UFState s, JobQueue dq) {
+    unsigned long long cnt = *dq.count;
+    if (cnt > dq.cap) cnt = dq.cap;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
+        KoutJob jb = dq.jobs[i];
+        Spin sp(s.cap);
+        uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
     }
 }
 

@@ -59,12 +59,13 @@ __device__ __forceinline__ u64w wmake(uint32_t rank, uint32_t par) { return ((u6
 struct Spin {
     uint32_t left;
     bool dead;
-    __device__ __forceinline__ explicit Spin(uint32_t cap) : left(cap), dead(false) {}
+    bool soft;   // a soft budget gives up quietly (the caller defers the operation)
+    __device__ __forceinline__ explicit Spin(uint32_t cap, bool soft_ = false) : left(cap), dead(false), soft(soft_) {}
     // One loop step; false once the operation must give up.
     __device__ __forceinline__ bool step(const UFState& s) {
         if (dead) return false;
         if (--left == 0) {
-            atomicOr(s.err, GC_DERR_NONCONV);
+            if (!soft) atomicOr(s.err, GC_DERR_NONCONV);
             dead = true;
             return false;
         }
