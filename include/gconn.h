@@ -189,6 +189,42 @@ gconn_status gconn_inc_labels(gconn_inc* h, uint32_t* labels, void* stream);
 /* Release the handle and its device memory (synchronises its last stream). */
 gconn_status gconn_inc_destroy(gconn_inc* h);
 
+/* --------------------------------------------------------------- serving */
+/* No paper counterpart for the loop itself; each request is an incremental
+ * insert or query batch (Section 3.5).  A server owns sessions (one
+ * device-resident union-find each, as gconn_inc) and a worker thread that
+ * admits submitted requests while device memory (cfg.device_budget_bytes of
+ * staging) and stream slots (cfg.slots) are free, coalesces consecutive
+ * requests of one session and kind (up to cfg.coalesce_pairs pairs) into one
+ * launch, and runs different sessions' launches concurrently.  Per session a
+ * query sees exactly the inserts submitted before it: a run of inserts, or of
+ * queries, starts only after the session's previous run finished.
+ * Requests use HOST buffers, which must stay valid until gconn_server_wait
+ * returns for that ticket; answers are written to `result` (uint8 per pair).
+ * gconn_server_wait blocks until the request completed and gives its latency
+ * (submit to answer available, host clock).  All calls are thread-safe. */
+enum { GCONN_OP_INSERT = 0, GCONN_OP_QUERY = 1 };
+typedef struct gconn_server_config {
+    uint64_t device_budget_bytes;  /* staging bytes allowed in flight (default 4 GiB) */
+    uint32_t slots;                /* concurrent launches / streams (default 8) */
+    uint32_t coalesce_pairs;       /* max pairs merged into one launch (default 2^22) */
+    uint32_t slot_pairs;           /* pinned staging per slot, in pairs (default 2^22) */
+    uint32_t reserved;
+} gconn_server_config;
+typedef struct gconn_server gconn_server;
+gconn_status gconn_server_config_default(gconn_server_config* c);
+gconn_status gconn_server_create(const gconn_server_config* cfg, gconn_server** out);
+gconn_status gconn_server_open_session(gconn_server* s, uint32_t n, const gconn_variant* v, uint32_t* session);
+gconn_status gconn_server_submit(gconn_server* s, uint32_t session, int op, uint64_t count,
+                                 const uint32_t* pairs, uint8_t* result, uint64_t* ticket);
+gconn_status gconn_server_wait(gconn_server* s, uint64_t ticket, double* latency_ms);
+/* Canonical labels of a session after every request submitted so far (host buffer). */
+gconn_status gconn_server_labels(gconn_server* s, uint32_t session, uint32_t* labels);
+gconn_status gconn_server_close_session(gconn_server* s, uint32_t session);
+gconn_status gconn_server_stats(gconn_server* s, uint64_t* launches, uint64_t* groups, uint64_t* requests);
+/* Finishes every submitted request, then releases everything. */
+gconn_status gconn_server_destroy(gconn_server* s);
+
 /* ----------------------------------------------------- captured plans */
 /* No paper counterpart.  The whole static pass for one input (the same work
  * as gconn_cc / gconn_cc_csr on the same arguments) captured once into a CUDA

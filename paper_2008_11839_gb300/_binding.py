@@ -77,6 +77,15 @@ class gconn_batch_tune(ctypes.Structure):
                 "link": list(self.link), "find": list(self.find)}
 
 
+GCONN_OP_INSERT, GCONN_OP_QUERY = 0, 1
+
+
+class gconn_server_config(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
+                ("coalesce_pairs", ctypes.c_uint32), ("slot_pairs", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
 class GconnError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -117,6 +126,15 @@ _SIGS = {
     "gconn_plan_run": (_i32, [_vp, _vp]),
     "gconn_plan_destroy": (_i32, [_vp]),
     "gconn_profile_sync": (_i32, []),
+    "gconn_server_config_default": (_i32, [ctypes.POINTER(gconn_server_config)]),
+    "gconn_server_create": (_i32, [ctypes.POINTER(gconn_server_config), ctypes.POINTER(_vp)]),
+    "gconn_server_open_session": (_i32, [_vp, _u32, ctypes.POINTER(gconn_variant), ctypes.POINTER(_u32)]),
+    "gconn_server_submit": (_i32, [_vp, _u32, _i32, _u64, _vp, _vp, ctypes.POINTER(_u64)]),
+    "gconn_server_wait": (_i32, [_vp, _u64, ctypes.POINTER(ctypes.c_double)]),
+    "gconn_server_labels": (_i32, [_vp, _u32, _vp]),
+    "gconn_server_close_session": (_i32, [_vp, _u32]),
+    "gconn_server_stats": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "gconn_server_destroy": (_i32, [_vp]),
     "gconn_sync": (_i32, [_vp]),
     "gconn_status_str": (ctypes.c_char_p, [_i32]),
     "gconn_launch_count": (_u64, []),
@@ -325,6 +343,55 @@ def gconn_plan_destroy(h):
 
 def gconn_profile_sync():
     check(lib().gconn_profile_sync(), "gconn_profile_sync")
+
+
+def gconn_server_config_default() -> gconn_server_config:
+    c = gconn_server_config()
+    check(lib().gconn_server_config_default(ctypes.byref(c)), "gconn_server_config_default")
+    return c
+
+
+def gconn_server_create(cfg=None):
+    h = ctypes.c_void_p()
+    check(lib().gconn_server_create(_vref(cfg), ctypes.byref(h)), "gconn_server_create")
+    return h
+
+
+def gconn_server_open_session(h, n, variant=None) -> int:
+    sid = ctypes.c_uint32()
+    check(lib().gconn_server_open_session(h, n, _vref(variant), ctypes.byref(sid)), "gconn_server_open_session")
+    return int(sid.value)
+
+
+def gconn_server_submit(h, session, op, count, pairs, result=None) -> int:
+    t = ctypes.c_uint64()
+    check(lib().gconn_server_submit(h, session, op, count, ptr(pairs), ptr(result), ctypes.byref(t)),
+          "gconn_server_submit")
+    return int(t.value)
+
+
+def gconn_server_wait(h, ticket) -> float:
+    ms = ctypes.c_double()
+    check(lib().gconn_server_wait(h, ticket, ctypes.byref(ms)), "gconn_server_wait")
+    return float(ms.value)
+
+
+def gconn_server_labels(h, session, labels):
+    check(lib().gconn_server_labels(h, session, ptr(labels)), "gconn_server_labels")
+
+
+def gconn_server_close_session(h, session):
+    check(lib().gconn_server_close_session(h, session), "gconn_server_close_session")
+
+
+def gconn_server_stats(h):
+    a, b_, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().gconn_server_stats(h, ctypes.byref(a), ctypes.byref(b_), ctypes.byref(c)), "gconn_server_stats")
+    return {"launches": int(a.value), "groups": int(b_.value), "requests": int(c.value)}
+
+
+def gconn_server_destroy(h):
+    check(lib().gconn_server_destroy(h), "gconn_server_destroy")
 
 
 def gconn_sync(stream=None):
