@@ -36,6 +36,7 @@ M_EDGES = 1 << 26
 SEED_STATIC = 0x6C0A0002          # per-config seed: base 0x6C0A0001 + config index
 SEED_INC = 0x6C0A0005
 SEED_BATCH = 0x6C0A0004
+SEED_SERVE = 0x6C0A0006
 INC_N_SCALE = 24
 INC_TOTAL = 1 << 28
 L2_FLUSH_BYTES = 256 << 20        # > 126 MB L2
@@ -318,6 +319,8 @@ def run_ours(args, rank, world, local_rank):
         result["incremental"] = run_incremental(g, torch, dev, stream, args)
     if rank == 0 and not args.no_batched:
         result["batched"] = run_batched(g, torch, dev, stream, args)
+    if rank == 0 and not args.no_serving:
+        result["serving"] = run_serving(g, torch, args)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(n, e, args.cpu_seconds)
     if dist:
@@ -440,6 +443,86 @@ def run_batched(g, torch, dev, stream, args):
     return res
 
 
+def run_serving(g, torch, args):
+    """8 sessions (n = 2^20 each), 64 requests per session alternating insert
+    and query batches of log-uniform size in [10^3, 10^5] (host buffers).
+    Plain form: one synchronous gconn_inc_* call per request in round-robin
+    order.  Served form: every session submits all its requests at once from
+    its own thread to one gconn_server.  Answers must be identical."""
+    import threading
+    S, R, n, scale = 8, 64, 1 << 20, 20
+    rng = np.random.default_rng(SEED_SERVE)
+    perm = graphgen.permutation(n, SEED_SERVE, 6)
+    streams = []
+    for s in range(S):
+        reqs, ip, qp = [], 0, 0
+        for r in range(R):
+            c = int(10 ** rng.uniform(3, 5))
+            if r % 2 == 0:
+                e = graphgen.rmat_range(scale, (s << 32) + ip, c, SEED_SERVE, perm=perm)
+                ip += c
+                reqs.append((g.GCONN_OP_INSERT, e))
+            else:
+                reqs.append((g.GCONN_OP_QUERY, graphgen.pairs_range(n, (s << 32) + qp, c, SEED_SERVE)))
+                qp += c
+        streams.append(reqs)
+    total_ops = sum(len(a) for reqs in streams for _, a in reqs)
+    v = g.make_variant(link="early")
+    # plain: one synchronous call per request
+    hs = [g.gconn_inc_create(n, v) for _ in range(S)]
+    torch.cuda.synchronize()
+    plain_ans = [[None] * R for _ in range(S)]
+    plain_lat = []
+    t0 = time.perf_counter()
+    for r in range(R):
+        for s in range(S):
+            op, a = streams[s][r]
+            t1 = time.perf_counter()
+            if op == g.GCONN_OP_INSERT:
+                g.gconn_inc_insert_batch(hs[s], len(a), a)
+            else:
+                out = np.empty(len(a), np.uint8)
+                g.gconn_inc_query(hs[s], len(a), a, out)
+                plain_ans[s][r] = out
+            plain_lat.append((time.perf_counter() - t1) * 1e3)
+    plain_s = time.perf_counter() - t0
+    for h in hs:
+        g.gconn_inc_destroy(h)
+    # served
+    srv = g.gconn_server_create()
+    sids = [g.gconn_server_open_session(srv, n, v) for _ in range(S)]
+    served_ans = [[None] * R for _ in range(S)]
+    lats = [[] for _ in range(S)]
+
+    def client(s):
+        ts = []
+        for r, (op, a) in enumerate(streams[s]):
+            out = np.empty(len(a), np.uint8) if op == g.GCONN_OP_QUERY else None
+            served_ans[s][r] = out
+            ts.append(g.gconn_server_submit(srv, sids[s], op, len(a), a, out))
+        lats[s] = [g.gconn_server_wait(srv, t) for t in ts]
+    th = [threading.Thread(target=client, args=(s,)) for s in range(S)]
+    t0 = time.perf_counter()
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    served_s = time.perf_counter() - t0
+    st = g.gconn_server_stats(srv)
+    g.gconn_server_destroy(srv)
+    same = all(served_ans[s][r] is None or bool((served_ans[s][r] == plain_ans[s][r]).all())
+               for s in range(S) for r in range(R))
+    all_lat = [x for l in lats for x in l]
+    return {"sessions": S, "requests": S * R, "ops": total_ops, "n_per_session": n,
+            "plain_ops_per_s": total_ops / plain_s, "served_ops_per_s": total_ops / served_s,
+            "speedup": round(plain_s / served_s, 2), "identical_answers": same,
+            "plain_latency_ms_p50": round(pct(plain_lat, 50), 3), "plain_latency_ms_p99": round(pct(plain_lat, 99), 3),
+            "served_latency_ms_p50": round(pct(all_lat, 50), 3), "served_latency_ms_p99": round(pct(all_lat, 99), 3),
+            "server_launches": st["launches"], "server_groups": st["groups"],
+            "latency": "host clock, submit to answers in the client's buffer (all requests submitted at once)",
+            "inputs": "host memory (pageable), copied through the server's pinned staging"}
+
+
 def cpu_baseline(n, e, seconds):
     """The oracle (sequential union-find, one host core) on the first m_s
     edges of the same edge list, m_s sized for about `seconds` of work."""
@@ -553,6 +636,7 @@ def main():
     ap.add_argument("--no-incremental", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-edges", type=int, default=M_EDGES)
