@@ -126,6 +126,16 @@ struct L2Window {
     ~L2Window();
 };
 
+// Device view of an incremental handle (for the serving loop's merged launches).
+struct IncView {
+    uint32_t n;
+    uint32_t* P;
+    uint32_t* H;
+    unsigned long long* W;
+    Variant v;
+};
+bool inc_view(const gconn_inc* h, IncView* out);
+
 // Staging of possibly-host arrays onto the device.
 gconn_status stage_in(const void* src, size_t bytes, cudaStream_t st, DevBuf& buf, const void** dev);
 

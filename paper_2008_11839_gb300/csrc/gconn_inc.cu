@@ -78,6 +78,16 @@ static gconn_status query_dispatch(const Variant& v, const UFState& s, const uin
 
 static UFState handle_state(gconn_inc* h) { return make_state(h->n, h->P, h->H, h->W, nullptr, h->v); }
 
+bool inc_view(const gconn_inc* h, IncView* out) {
+    if (!h || !out) return false;
+    out->n = h->n;
+    out->P = h->P;
+    out->H = h->H;
+    out->W = h->W;
+    out->v = h->v;
+    return true;
+}
+
 }  // namespace gc
 
 extern "C" gconn_status gconn_inc_create(uint32_t n, const gconn_variant* vin, void* stream, gconn_inc** out) {

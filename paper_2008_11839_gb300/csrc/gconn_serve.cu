@@ -1,21 +1,29 @@
 // gconn_serve.cu -- a serving loop over device-resident incremental
 // connectivity (Section 3.5): clients submit insert and query batches for
-// sessions (one union-find forest each); a worker thread admits them as
-// device memory and stream slots free up, coalesces consecutive requests of
-// the same session and kind into one launch, runs different sessions'
-// launches concurrently on separate streams, and completes each request with
-// its host-measured latency.
+// sessions (one union-find forest each); a worker thread runs scheduler
+// steps.  Each step takes, from every session that may proceed, the run of
+// pending requests at the head of its queue that share one kind (insert or
+// query), packs all of them -- across sessions -- into one pinned staging
+// buffer, and processes them with one host-to-device copy, one multi-forest
+// kernel per union rule present (every thread finds its request's segment and
+// works in that session's forest), and one device-to-host copy of the
+// answers.  Steps alternate between streams, so one step's copies and kernels
+// overlap the next one's staging.  Admission is bounded by a device-memory
+// budget and by the number of steps in flight.
 //
-// Ordering per session keeps the incremental semantics exact: requests form
-// phases of consecutive inserts or consecutive queries; a phase starts only
-// after the previous phase of that session has finished on the device, so a
+// Exactness per session: requests form phases of consecutive inserts or
+// consecutive queries; a session joins a step only with requests of the phase
+// it already has in flight (or any phase when it has nothing in flight), so a
 // query sees exactly the inserts submitted before it.  Inserts of one phase
-// commute and queries of one phase only compress, so coalescing and running
-// them together changes no answer.
+// commute and queries of one phase only compress paths, so packing and
+// concurrency change no answer.  Requests larger than a step's staging and
+// sessions with round-based finishes (SV, Liu-Tarjan) run through their
+// handle's own calls as a step of their own.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -26,10 +34,15 @@
 #include <vector>
 
 #include "gc_internal.h"
+#include "gc_static.h"
+#include "uf_device.cuh"
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
+using namespace gc;
+
+constexpr uint32_t MAX_SEGS = 4096;   // requests per merged step
 
 struct Request {
     uint64_t ticket;
@@ -41,36 +54,121 @@ struct Request {
     Clock::time_point submitted;
 };
 
-struct Group;
-
 struct Session {
     uint32_t id;
     gconn_inc* h = nullptr;
+    IncView view;
+    bool mergeable = false;       // union-find finish: can join merged steps
     std::deque<Request> pending;
-    int inflight_phase = -1;      // op of the groups in flight, -1 = none
-    int inflight_groups = 0;
+    int inflight_phase = -1;      // kind of the work in flight, -1 = none
+    int inflight = 0;             // steps holding this session's requests
     bool closing = false;
 };
 
-struct Slot {
+// One segment of a merged step: a request's pairs inside the step.
+struct Seg {
+    unsigned long long start;     // first pair of the segment in its launch range
+    unsigned long long out;       // first answer slot (queries)
+    uint32_t* P;
+    uint32_t* H;
+    unsigned long long* W;
+    uint32_t n, op, cap, seed;
+};
+
+struct StepBuf {
     cudaStream_t st = nullptr;
-    uint32_t* h_in = nullptr;     // pinned staging (pairs)
-    uint8_t* h_out = nullptr;     // pinned staging (query answers)
+    uint32_t* h_pairs = nullptr;  // pinned
+    uint8_t* h_out = nullptr;     // pinned
+    Seg* h_segs = nullptr;        // pinned
+    uint32_t* h_err = nullptr;    // pinned
     bool busy = false;
 };
 
-struct Group {
-    uint32_t session;
-    int op;
-    int slot;
+struct Step {
+    int buf = -1;
+    bool solo = false;            // one request through its handle's own calls
     std::vector<Request> reqs;
-    uint64_t total = 0;           // pairs in the group
-    uint64_t bytes = 0;           // device bytes held
-    void* d_in = nullptr;
-    uint8_t* d_out = nullptr;
+    std::vector<uint32_t> seg_of; // request -> its answer offset (queries)
+    uint64_t total = 0, answers = 0, bytes = 0;
     cudaEvent_t done = nullptr;
     gconn_status status = GCONN_OK;
 };
+
+// Multi-forest union / query over one launch range of a merged step.
+template <int L, int F, int S>
+__global__ void __launch_bounds__(256) k_serve(const uint2* __restrict__ pairs, unsigned long long total,
+                                               const Seg* __restrict__ segs, uint32_t nseg, uint8_t* out,
+                                               uint32_t* err) {
+    __shared__ unsigned long long sstart[MAX_SEGS];
+    bool cached = nseg <= MAX_SEGS;
+    if (cached)
+        for (uint32_t i = threadIdx.x; i < nseg; i += blockDim.x) sstart[i] = segs[i].start;
+    __syncthreads();
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        uint32_t lo = 0, hi = nseg;   // last segment with start <= i
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            unsigned long long sm = cached ? sstart[mid] : segs[mid].start;
+            if (sm <= i) lo = mid; else hi = mid;
+        }
+        const Seg& g = segs[lo];
+        UFState s;
+        s.P = g.P; s.H = g.H; s.W = g.W; s.sf = nullptr; s.err = err; s.n = g.n; s.cap = g.cap; s.seed = g.seed;
+        uint2 e = __ldcs(pairs + i);
+        bool inrange = e.x < g.n && e.y < g.n;
+        if (!inrange) atomicOr(err, GC_DERR_RANGE);
+        Spin sp(g.cap);
+        if (g.op == GCONN_OP_INSERT) {
+            if (inrange && e.x != e.y) uf_union<L, F, S, false>(s, e.x, e.y, 0, sp);
+        } else {
+            uint8_t a = 0;
+            if (inrange) {
+                if (L == LK_JTB) a = jtb_find<F>(s, e.x, sp) == jtb_find<F>(s, e.y, sp);
+                else a = uf_find<F, true>(s, e.x, sp) == uf_find<F, true>(s, e.y, sp);
+            }
+            out[g.out + (i - g.start)] = a;
+        }
+    }
+}
+
+int rule_key(const Variant& v) {
+    int L, F, S;
+    uf_triple(v, &L, &F, &S);
+    return (L << 8) | (F << 4) | S;
+}
+
+template <class Fn>
+gconn_status dispatch_rule(int key, Fn&& fn) {
+    int L = key >> 8, F = (key >> 4) & 15, S = key & 15;
+#define GC_SV_CASE(l, f, s) \
+    if (L == l && F == f && S == s) return fn.template operator()<l, f, s>();
+    GC_SV_CASE(LK_ASYNC, FD_NAIVE, SP_NONE)
+    GC_SV_CASE(LK_ASYNC, FD_COMPRESS, SP_NONE)
+    GC_SV_CASE(LK_ASYNC, FD_SPLIT, SP_NONE)
+    GC_SV_CASE(LK_ASYNC, FD_HALVE, SP_NONE)
+    GC_SV_CASE(LK_HOOKS, FD_NAIVE, SP_NONE)
+    GC_SV_CASE(LK_HOOKS, FD_COMPRESS, SP_NONE)
+    GC_SV_CASE(LK_HOOKS, FD_SPLIT, SP_NONE)
+    GC_SV_CASE(LK_HOOKS, FD_HALVE, SP_NONE)
+    GC_SV_CASE(LK_EARLY, FD_NAIVE, SP_NONE)
+    GC_SV_CASE(LK_EARLY, FD_COMPRESS, SP_NONE)
+    GC_SV_CASE(LK_EARLY, FD_SPLIT, SP_NONE)
+    GC_SV_CASE(LK_EARLY, FD_HALVE, SP_NONE)
+    GC_SV_CASE(LK_REMCAS, FD_NAIVE, SP_SPLIT_ONE)
+    GC_SV_CASE(LK_REMCAS, FD_NAIVE, SP_HALVE_ONE)
+    GC_SV_CASE(LK_REMCAS, FD_NAIVE, SP_SPLICE)
+    GC_SV_CASE(LK_REMCAS, FD_SPLIT, SP_SPLIT_ONE)
+    GC_SV_CASE(LK_REMCAS, FD_SPLIT, SP_HALVE_ONE)
+    GC_SV_CASE(LK_REMCAS, FD_SPLIT, SP_SPLICE)
+    GC_SV_CASE(LK_REMCAS, FD_HALVE, SP_SPLIT_ONE)
+    GC_SV_CASE(LK_REMCAS, FD_HALVE, SP_HALVE_ONE)
+    GC_SV_CASE(LK_REMCAS, FD_HALVE, SP_SPLICE)
+    GC_SV_CASE(LK_JTB, FD_NAIVE, SP_NONE)
+    GC_SV_CASE(LK_JTB, FD_TWOTRY, SP_NONE)
+#undef GC_SV_CASE
+    return GCONN_E_UNSUPPORTED;
+}
 
 }  // namespace
 
@@ -83,168 +181,241 @@ struct gconn_server {
     bool stop = false;
     uint64_t next_ticket = 1;
     uint32_t next_session = 1;
+    uint32_t rr = 0;              // round-robin start among sessions
     std::map<uint32_t, Session> sessions;
-    std::vector<Slot> slots;
-    std::deque<std::unique_ptr<Group>> inflight;
+    std::vector<StepBuf> bufs;
+    std::deque<std::unique_ptr<Step>> inflight;
     uint64_t bytes_inflight = 0;
     struct Done {
         gconn_status status;
         double latency_ms;
     };
     std::map<uint64_t, Done> done;
-    uint64_t launches = 0, groups = 0, requests_done = 0;
+    uint64_t launches = 0, steps = 0, requests_done = 0;
 };
 
 namespace {
 
-using namespace gc;
-
-// Launch a formed group on its slot (called by the worker without the lock
-// held for the CUDA calls; the group is owned by the worker until completion).
-gconn_status launch_group(gconn_server* S, Session& ses, Group& g) {
-    Slot& sl = S->slots[g.slot];
-    cudaStream_t st = sl.st;
-    const uint64_t cap = S->cfg.slot_pairs;
-    GC_CUDA(cudaMallocAsync(&g.d_in, sizeof(uint32_t) * 2 * g.total, st));
-    if (g.op == GCONN_OP_QUERY) GC_CUDA(cudaMallocAsync((void**)&g.d_out, g.total, st));
-    // pack the requests' pairs into the slot's pinned buffer; one host-to-device
-    // copy per full buffer (the buffer is reused only after its copy finished)
-    uint64_t fill = 0, dev_pos = 0;
-    auto flush = [&]() -> gconn_status {
-        if (!fill) return GCONN_OK;
-        GC_CUDA(cudaMemcpyAsync((uint32_t*)g.d_in + 2 * dev_pos, sl.h_in, sizeof(uint32_t) * 2 * fill,
-                                cudaMemcpyHostToDevice, st));
-        dev_pos += fill;
-        fill = 0;
-        return GCONN_OK;
-    };
-    for (const Request& r : g.reqs) {
-        uint64_t done = 0;
-        while (done < r.count) {
-            if (fill == cap) {
-                GC_TRY(flush());
-                GC_CUDA(cudaStreamSynchronize(st));
-            }
-            uint64_t c = r.count - done < cap - fill ? r.count - done : cap - fill;
-            memcpy(sl.h_in + 2 * fill, r.pairs + 2 * done, sizeof(uint32_t) * 2 * c);
-            fill += c;
-            done += c;
-        }
-    }
-    GC_TRY(flush());
-    if (g.op == GCONN_OP_INSERT) {
-        GC_TRY(gconn_inc_insert_batch(ses.h, g.total, (const uint32_t*)g.d_in, st));
-    } else {
-        GC_TRY(gconn_inc_query(ses.h, g.total, (const uint32_t*)g.d_in, g.d_out, st));
-    }
-    S->launches++;
-    GC_CUDA(cudaFreeAsync(g.d_in, st));
-    GC_CUDA(cudaEventRecord(g.done, st));
+gconn_status status_of_err(uint32_t e) {
+    if (e & GC_DERR_RANGE) return GCONN_E_RANGE;
+    if (e & GC_DERR_NONCONV) return GCONN_E_NONCONVERGED;
     return GCONN_OK;
 }
 
-// Copy a finished query group's answers back to each request's buffer.
-gconn_status finish_group(gconn_server* S, Group& g) {
-    Slot& sl = S->slots[g.slot];
-    if (g.op != GCONN_OP_QUERY || g.status != GCONN_OK) {
-        if (g.d_out) cudaFreeAsync(g.d_out, sl.st);
-        return g.status;
-    }
-    const uint64_t cap = S->cfg.slot_pairs;
-    uint64_t pos = 0;
-    for (const Request& r : g.reqs) {
-        uint64_t done = 0;
-        while (done < r.count) {
-            uint64_t c = r.count - done < cap ? r.count - done : cap;
-            GC_CUDA(cudaMemcpyAsync(sl.h_out, g.d_out + pos + done, c, cudaMemcpyDeviceToHost, sl.st));
-            GC_CUDA(cudaStreamSynchronize(sl.st));
-            memcpy(r.result + done, sl.h_out, c);
-            done += c;
-        }
+// A merged step: stage every request's pairs (grouped by union rule), copy
+// once, launch per rule, copy the answers back, all on the buffer's stream.
+gconn_status launch_merged(gconn_server* S, Step& sp, std::vector<Session*>& owners) {
+    StepBuf& b = S->bufs[sp.buf];
+    cudaStream_t st = b.st;
+    // group requests by rule so each rule's pairs are contiguous
+    std::vector<size_t> idx(sp.reqs.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::vector<int> key(sp.reqs.size());
+    for (size_t i = 0; i < idx.size(); ++i) key[i] = rule_key(owners[i]->view.v);
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t c) { return key[a] < key[c]; });
+    sp.seg_of.assign(sp.reqs.size(), 0);
+    uint64_t pos = 0, ans = 0;
+    for (size_t j = 0; j < idx.size(); ++j) {
+        const Request& r = sp.reqs[idx[j]];
+        memcpy(b.h_pairs + 2 * pos, r.pairs, sizeof(uint32_t) * 2 * r.count);
+        const IncView& v = owners[idx[j]]->view;
+        Seg& g = b.h_segs[j];
+        g.start = pos;
+        g.out = ans;
+        g.P = v.P; g.H = v.H; g.W = v.W;
+        g.n = v.n;
+        g.op = (uint32_t)r.op;
+        g.cap = v.v.cap;
+        g.seed = (uint32_t)(v.v.seed ^ (v.v.seed >> 32));
+        sp.seg_of[idx[j]] = (uint32_t)ans;
+        if (r.op == GCONN_OP_QUERY) ans += r.count;
         pos += r.count;
     }
-    GC_CUDA(cudaFreeAsync(g.d_out, sl.st));
+    sp.total = pos;
+    sp.answers = ans;
+    size_t nseg = idx.size();
+    // launch ranges: one per union rule; segment starts become relative to
+    // their range before the table is copied (once)
+    std::vector<std::pair<size_t, size_t>> ranges;
+    std::vector<uint64_t> r0s;
+    for (size_t a = 0; a < nseg;) {
+        size_t c = a;
+        while (c < nseg && key[idx[c]] == key[idx[a]]) ++c;
+        ranges.push_back({a, c});
+        r0s.push_back(b.h_segs[a].start);
+        a = c;
+    }
+    for (size_t r = 0; r < ranges.size(); ++r)
+        for (size_t j = ranges[r].first; j < ranges[r].second; ++j) b.h_segs[j].start -= r0s[r];
+    size_t seg_bytes = sizeof(Seg) * nseg;
+    // one device block: pairs | answers | segments | error word
+    size_t off_out = sizeof(uint32_t) * 2 * pos;
+    size_t off_seg = (off_out + ans + 255) & ~(size_t)255;
+    size_t off_err = off_seg + seg_bytes;
+    char* d = nullptr;
+    GC_CUDA(cudaMallocAsync((void**)&d, off_err + 16, st));
+    GC_CUDA(cudaMemsetAsync(d + off_err, 0, sizeof(uint32_t), st));
+    GC_CUDA(cudaMemcpyAsync(d, b.h_pairs, off_out, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemcpyAsync(d + off_seg, b.h_segs, seg_bytes, cudaMemcpyHostToDevice, st));
+    uint32_t* d_err = (uint32_t*)(d + off_err);
+    const Seg* d_segs = (const Seg*)(d + off_seg);
+    uint8_t* d_out = (uint8_t*)(d + off_out);
+    for (size_t r = 0; r < ranges.size(); ++r) {
+        size_t a = ranges[r].first, c = ranges[r].second;
+        uint64_t r0 = r0s[r], r1 = r + 1 < ranges.size() ? r0s[r + 1] : pos;
+        const uint2* rp = (const uint2*)d + r0;
+        GC_TRY(dispatch_rule(key[idx[a]], [&]<int l, int f, int k2>() {
+            auto k = k_serve<l, f, k2>;
+            return launch("serve", k, grid_for(k, 256, r1 - r0), 256, 0, st, rp, (unsigned long long)(r1 - r0),
+                          d_segs + a, (uint32_t)(c - a), d_out, d_err);
+        }));
+        S->launches++;
+    }
+    if (ans) GC_CUDA(cudaMemcpyAsync(b.h_out, d + off_out, ans, cudaMemcpyDeviceToHost, st));
+    GC_CUDA(cudaMemcpyAsync(b.h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    GC_CUDA(cudaFreeAsync(d, st));
+    GC_CUDA(cudaEventRecord(sp.done, st));
     return GCONN_OK;
+}
+
+// A solo step: one request through its handle's own calls (host buffers).
+gconn_status launch_solo(gconn_server* S, Step& sp, Session& ses) {
+    const Request& r = sp.reqs[0];
+    cudaStream_t st = S->bufs[sp.buf].st;
+    gconn_status s;
+    if (r.op == GCONN_OP_INSERT) s = gconn_inc_insert_batch(ses.h, r.count, r.pairs, st);
+    else s = gconn_inc_query(ses.h, r.count, r.pairs, r.result, st);
+    S->launches++;
+    cudaEventRecord(sp.done, st);
+    return s;
 }
 
 void worker_loop(gconn_server* S) {
     cudaSetDevice(S->device);
+    const uint64_t C = S->cfg.slot_pairs;
     std::unique_lock<std::mutex> lk(S->mu);
     while (true) {
         // 1. completions
         bool progressed = false;
         for (auto it = S->inflight.begin(); it != S->inflight.end();) {
-            Group& g = **it;
-            cudaError_t q = cudaEventQuery(g.done);
+            Step& sp = **it;
+            cudaError_t q = cudaEventQuery(sp.done);
             if (q == cudaErrorNotReady) {
                 ++it;
                 continue;
             }
-            lk.unlock();
-            if (q != cudaSuccess) g.status = cuda_status(q);
-            gconn_status fs = finish_group(S, g);
-            gconn_status es = read_and_clear_err(S->slots[g.slot].st);
-            lk.lock();
-            if (g.status == GCONN_OK) g.status = fs != GCONN_OK ? fs : es;
-            auto now = Clock::now();
-            for (const Request& r : g.reqs) {
-                double ms = std::chrono::duration<double, std::milli>(now - r.submitted).count();
-                S->done[r.ticket] = {g.status, ms};
-                S->requests_done++;
+            StepBuf& b = S->bufs[sp.buf];
+            if (q != cudaSuccess && sp.status == GCONN_OK) sp.status = cuda_status(q);
+            if (!sp.solo && sp.status == GCONN_OK) {
+                sp.status = status_of_err(*b.h_err);
+                for (size_t i = 0; i < sp.reqs.size(); ++i) {
+                    const Request& r = sp.reqs[i];
+                    if (r.op == GCONN_OP_QUERY) memcpy(r.result, b.h_out + sp.seg_of[i], r.count);
+                }
             }
-            S->slots[g.slot].busy = false;
-            S->bytes_inflight -= g.bytes;
-            Session& ses = S->sessions[g.session];
-            if (--ses.inflight_groups == 0) ses.inflight_phase = -1;
-            cudaEventDestroy(g.done);
+            auto now = Clock::now();
+            for (const Request& r : sp.reqs) {
+                double ms = std::chrono::duration<double, std::milli>(now - r.submitted).count();
+                S->done[r.ticket] = {sp.status, ms};
+                S->requests_done++;
+                Session& ses = S->sessions[r.session];
+                if (--ses.inflight == 0) ses.inflight_phase = -1;
+            }
+            b.busy = false;
+            S->bytes_inflight -= sp.bytes;
+            cudaEventDestroy(sp.done);
             it = S->inflight.erase(it);
             progressed = true;
         }
         if (progressed) S->cv_done.notify_all();
-        // 2. admissions: round-robin over sessions, one group per session per pass
+        // 2. new steps while staging buffers are free
         bool launched = false;
-        for (auto& kv : S->sessions) {
-            Session& ses = kv.second;
-            if (ses.pending.empty()) continue;
-            int op = ses.pending.front().op;
-            if (ses.inflight_phase != -1 && ses.inflight_phase != op) continue;   // previous phase still running
-            int slot = -1;
-            for (size_t i = 0; i < S->slots.size(); ++i)
-                if (!S->slots[i].busy) { slot = (int)i; break; }
-            if (slot < 0) break;
-            auto g = std::make_unique<Group>();
-            g->session = ses.id;
-            g->op = op;
-            g->slot = slot;
-            while (!ses.pending.empty() && ses.pending.front().op == op) {
-                const Request& r = ses.pending.front();
-                uint64_t need = (sizeof(uint32_t) * 2 + (op == GCONN_OP_QUERY ? 1 : 0)) * r.count;
-                bool first = g->reqs.empty();
-                if (!first && (g->total + r.count > S->cfg.coalesce_pairs ||
-                               S->bytes_inflight + g->bytes + need > S->cfg.device_budget_bytes))
-                    break;
-                if (first && S->bytes_inflight > 0 && S->bytes_inflight + need > S->cfg.device_budget_bytes)
-                    break;   // wait for memory (a lone request larger than the budget still runs alone)
-                g->reqs.push_back(r);
-                g->total += r.count;
-                g->bytes += need;
-                ses.pending.pop_front();
-            }
-            if (g->reqs.empty()) continue;
-            S->slots[slot].busy = true;
-            S->bytes_inflight += g->bytes;
-            ses.inflight_phase = op;
-            ses.inflight_groups++;
-            S->groups++;
-            cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);
-            Group* gp = g.get();
-            S->inflight.push_back(std::move(g));
+        auto free_buf = [&]() -> int {
+            for (size_t i = 0; i < S->bufs.size(); ++i)
+                if (!S->bufs[i].busy) return (int)i;
+            return -1;
+        };
+        auto start_step = [&](std::unique_ptr<Step> sp, std::vector<Session*> owners) {
+            S->bufs[sp->buf].busy = true;
+            S->bytes_inflight += sp->bytes;
+            S->steps++;
+            cudaEventCreateWithFlags(&sp->done, cudaEventDisableTiming);
+            Step* p = sp.get();
+            S->inflight.push_back(std::move(sp));
             lk.unlock();
-            gp->status = launch_group(S, ses, *gp);
-            if (gp->status != GCONN_OK) cudaEventRecord(gp->done, S->slots[slot].st);
+            gconn_status ls = p->solo ? launch_solo(S, *p, *owners[0]) : launch_merged(S, *p, owners);
+            if (ls != GCONN_OK) {
+                cudaGetLastError();
+                p->status = ls;
+                cudaEventRecord(p->done, S->bufs[p->buf].st);
+            }
             lk.lock();
             launched = true;
+        };
+        size_t ns = S->sessions.size();
+        // 2a. one request that cannot be merged (round-based finish, or larger
+        //     than a step's staging) runs as a step of its own
+        if (ns) {
+            auto it = S->sessions.begin();
+            std::advance(it, S->rr % ns);
+            for (size_t visited = 0; visited < ns; ++visited, ++it) {
+                if (it == S->sessions.end()) it = S->sessions.begin();
+                Session& ses = it->second;
+                if (ses.pending.empty()) continue;
+                const Request& r = ses.pending.front();
+                if (ses.inflight_phase != -1 && ses.inflight_phase != r.op) continue;
+                if (ses.mergeable && r.count <= C) continue;
+                uint64_t need = (sizeof(uint32_t) * 2 + (r.op == GCONN_OP_QUERY ? 1 : 0)) * r.count;
+                if (S->bytes_inflight && S->bytes_inflight + need > S->cfg.device_budget_bytes) break;
+                int bi = free_buf();
+                if (bi < 0) break;
+                auto sp = std::make_unique<Step>();
+                sp->buf = bi;
+                sp->solo = true;
+                sp->reqs.push_back(r);
+                sp->bytes = need;
+                ses.pending.pop_front();
+                ses.inflight_phase = r.op;
+                ses.inflight += 1;
+                start_step(std::move(sp), std::vector<Session*>{&ses});
+                break;
+            }
         }
+        // 2b. one merged step over every session that may proceed
+        int bi = free_buf();
+        ns = S->sessions.size();
+        if (bi >= 0 && ns) {
+            auto sp = std::make_unique<Step>();
+            sp->buf = bi;
+            std::vector<Session*> owners;
+            auto it = S->sessions.begin();
+            std::advance(it, S->rr % ns);
+            for (size_t visited = 0; visited < ns; ++visited, ++it) {
+                if (it == S->sessions.end()) it = S->sessions.begin();
+                Session& ses = it->second;
+                if (ses.pending.empty() || !ses.mergeable) continue;
+                int op = ses.pending.front().op;
+                if (ses.inflight_phase != -1 && ses.inflight_phase != op) continue;
+                while (!ses.pending.empty() && ses.pending.front().op == op && sp->reqs.size() < MAX_SEGS) {
+                    const Request& r = ses.pending.front();
+                    if (r.count > C || sp->total + r.count > C) break;
+                    uint64_t need = (sizeof(uint32_t) * 2 + (op == GCONN_OP_QUERY ? 1 : 0)) * r.count;
+                    if (S->bytes_inflight + sp->bytes + need > S->cfg.device_budget_bytes &&
+                        !(S->bytes_inflight == 0 && sp->reqs.empty()))
+                        break;
+                    sp->reqs.push_back(r);
+                    owners.push_back(&ses);
+                    sp->total += r.count;
+                    sp->bytes += need;
+                    ses.pending.pop_front();
+                    ses.inflight_phase = op;
+                    ses.inflight += 1;
+                }
+                if (sp->total >= C || sp->reqs.size() >= MAX_SEGS) break;
+            }
+            if (!sp->reqs.empty()) start_step(std::move(sp), owners);
+        }
+        S->rr++;
         if (S->stop && S->inflight.empty()) {
             bool any = false;
             for (auto& kv : S->sessions) any |= !kv.second.pending.empty();
@@ -252,7 +423,11 @@ void worker_loop(gconn_server* S) {
         }
         if (!launched && !progressed) {
             if (S->inflight.empty()) S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
-            else S->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            else {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(5));
+                lk.lock();
+            }
         }
     }
 }
@@ -262,9 +437,10 @@ void worker_loop(gconn_server* S) {
 extern "C" gconn_status gconn_server_config_default(gconn_server_config* c) {
     if (!c) return GCONN_E_INVAL;
     c->device_budget_bytes = 4ull << 30;
-    c->slots = 8;
+    c->slots = 3;
     c->coalesce_pairs = 1u << 22;
     c->slot_pairs = 1u << 22;
+    c->reserved = 0;
     return GCONN_OK;
 }
 
@@ -274,8 +450,7 @@ extern "C" gconn_status gconn_server_create(const gconn_server_config* cfg, gcon
     gconn_server_config c;
     gconn_server_config_default(&c);
     if (cfg) c = *cfg;
-    if (c.slots < 1 || c.slots > 64 || c.slot_pairs < 1024 || c.coalesce_pairs < 1 || c.device_budget_bytes < 1)
-        return GCONN_E_INVAL;
+    if (c.slots < 1 || c.slots > 64 || c.slot_pairs < 1024 || c.device_budget_bytes < 1) return GCONN_E_INVAL;
     gconn_server* S = new gconn_server();
     S->cfg = c;
     cudaGetDevice(&S->device);
@@ -283,11 +458,13 @@ extern "C" gconn_status gconn_server_create(const gconn_server_config* cfg, gcon
         delete S;
         return GCONN_E_CUDA;
     }
-    S->slots.resize(c.slots);
-    for (Slot& sl : S->slots) {
-        if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaMallocHost(&sl.h_in, sizeof(uint32_t) * 2 * c.slot_pairs) != cudaSuccess ||
-            cudaMallocHost(&sl.h_out, c.slot_pairs) != cudaSuccess) {
+    S->bufs.resize(c.slots);
+    for (StepBuf& b : S->bufs) {
+        if (cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMallocHost(&b.h_pairs, sizeof(uint32_t) * 2 * (size_t)c.slot_pairs) != cudaSuccess ||
+            cudaMallocHost(&b.h_out, c.slot_pairs) != cudaSuccess ||
+            cudaMallocHost(&b.h_segs, sizeof(Seg) * MAX_SEGS) != cudaSuccess ||
+            cudaMallocHost(&b.h_err, sizeof(uint32_t)) != cudaSuccess) {
             gconn_server_destroy(S);
             return GCONN_E_NOMEM;
         }
@@ -316,6 +493,8 @@ extern "C" gconn_status gconn_server_open_session(gconn_server* S, uint32_t n, c
     Session& ses = S->sessions[id];
     ses.id = id;
     ses.h = h;
+    inc_view(h, &ses.view);
+    ses.mergeable = ses.view.v.link != GCONN_LINK_SV && ses.view.v.link != GCONN_LINK_LT;
     *session = id;
     return GCONN_OK;
 }
@@ -360,7 +539,7 @@ extern "C" gconn_status gconn_server_labels(gconn_server* S, uint32_t session, u
         // drain the session first: its labels reflect every request submitted so far
         S->cv_done.wait(lk, [&] {
             Session& ses = S->sessions[session];
-            return ses.pending.empty() && ses.inflight_groups == 0;
+            return ses.pending.empty() && ses.inflight == 0;
         });
         h = it->second.h;
     }
@@ -383,7 +562,7 @@ extern "C" gconn_status gconn_server_close_session(gconn_server* S, uint32_t ses
         it->second.closing = true;
         S->cv_done.wait(lk, [&] {
             Session& ses = S->sessions[session];
-            return ses.pending.empty() && ses.inflight_groups == 0;
+            return ses.pending.empty() && ses.inflight == 0;
         });
         h = S->sessions[session].h;
         S->sessions.erase(session);
@@ -396,7 +575,7 @@ extern "C" gconn_status gconn_server_stats(gconn_server* S, uint64_t* launches, 
     if (!S) return GCONN_E_INVAL;
     std::lock_guard<std::mutex> lk(S->mu);
     if (launches) *launches = S->launches;
-    if (groups) *groups = S->groups;
+    if (groups) *groups = S->steps;
     if (requests) *requests = S->requests_done;
     return GCONN_OK;
 }
@@ -414,13 +593,15 @@ extern "C" gconn_status gconn_server_destroy(gconn_server* S) {
     cudaSetDevice(S->device);
     for (auto& kv : S->sessions)
         if (kv.second.h) gconn_inc_destroy(kv.second.h);
-    for (Slot& sl : S->slots) {
-        if (sl.st) {
-            cudaStreamSynchronize(sl.st);
-            cudaStreamDestroy(sl.st);
+    for (StepBuf& b : S->bufs) {
+        if (b.st) {
+            cudaStreamSynchronize(b.st);
+            cudaStreamDestroy(b.st);
         }
-        if (sl.h_in) cudaFreeHost(sl.h_in);
-        if (sl.h_out) cudaFreeHost(sl.h_out);
+        if (b.h_pairs) cudaFreeHost(b.h_pairs);
+        if (b.h_out) cudaFreeHost(b.h_out);
+        if (b.h_segs) cudaFreeHost(b.h_segs);
+        if (b.h_err) cudaFreeHost(b.h_err);
     }
     cudaSetDevice(prev);
     delete S;
