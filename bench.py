@@ -121,7 +121,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------ input build
 def make_static_input(rank: int, scale: int = SCALE, m: int = M_EDGES):
-    seed = SEED_STATIC + 1000 * rank
+    seed = replica_seed(rank)
     e = graphgen.rmat(scale, m, seed)
     n = 1 << scale
     off, cols = graphgen.csr(n, e)
@@ -173,6 +173,22 @@ def pct(xs, p):
     k = (len(xs) - 1) * p / 100.0
     lo, hi = int(np.floor(k)), int(np.ceil(k))
     return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+# ------------------------------------------------------------ ranks
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """Slowest rank's time: the whole job is done only when every replica is."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank's replica graph: same shape, its own seed."""
+    return SEED_STATIC + 1000 * rank
 
 
 # ------------------------------------------------------------ our arm
@@ -262,11 +278,7 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     step_ms = [s.elapsed_time(x) for s, x in zip(starts, ends)]
-    ms = float(np.mean(step_ms))
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(step_ms)), dist, dev)
     g.gconn_plan_destroy(plan)
 
     # dominant kernel's roofline from the live per-kernel events
