@@ -60,11 +60,16 @@ typedef enum gconn_status {
  * needs CSR input: the skip rule drops whole adjacency lists. */
 enum { GCONN_SAMPLE_NONE = 0, GCONN_SAMPLE_KOUT = 1, GCONN_SAMPLE_HB = 2, GCONN_SAMPLE_BFS = 3 };
 
-/* Finish algorithm (Section 3.4): union-find rules (Algorithms 7-9, 11 and
- * Union-JTB), root-based Shiloach-Vishkin (Algorithm 12), Liu-Tarjan. */
+/* Finish algorithm (Section 3.4): union-find rules (Algorithms 7-11 and
+ * Union-JTB), the finish rules of ECL-CC (Union-Async with path splitting)
+ * and Afforest, root-based Shiloach-Vishkin (Algorithm 12), Liu-Tarjan,
+ * Label Propagation and Stergiou's algorithm.  LP and Stergiou are not
+ * root-based: components only (no forest, no incremental handle). */
 enum {
     GCONN_LINK_ASYNC = 0, GCONN_LINK_HOOKS = 1, GCONN_LINK_EARLY = 2,
-    GCONN_LINK_REMCAS = 3, GCONN_LINK_JTB = 4, GCONN_LINK_SV = 5, GCONN_LINK_LT = 6
+    GCONN_LINK_REMCAS = 3, GCONN_LINK_JTB = 4, GCONN_LINK_SV = 5, GCONN_LINK_LT = 6,
+    GCONN_LINK_REMLOCK = 7, GCONN_LINK_ECLCC = 8, GCONN_LINK_AFFOREST = 9,
+    GCONN_LINK_LP = 10, GCONN_LINK_STERGIOU = 11
 };
 
 /* On-the-fly compression (Algorithm 5).  FULLSHORTCUT = no on-the-fly
@@ -76,7 +81,7 @@ enum {
     GCONN_FIND_HALVE = 3, GCONN_FIND_TWOTRYSPLIT = 4, GCONN_FIND_FULLSHORTCUT = 5
 };
 
-/* Splice step of Union-Rem-CAS (Algorithm 6); NONE selects SPLICE for Rem. */
+/* Splice step of Rem's algorithms (Algorithm 6); NONE selects SPLICE. */
 enum { GCONN_SPLICE_NONE = 0, GCONN_SPLICE_SPLIT_ONE = 1, GCONN_SPLICE_HALVE_ONE = 2, GCONN_SPLICE_SPLICE = 3 };
 
 /* Liu-Tarjan rule set (appendix list of 16 variants): connect rule in the
@@ -92,7 +97,7 @@ typedef struct gconn_variant {
     int32_t hb_n;       /* HB: edges per remaining root (default 4) */
     int32_t link;       /* GCONN_LINK_* */
     int32_t find;       /* GCONN_FIND_* */
-    int32_t splice;     /* GCONN_SPLICE_* (Union-Rem-CAS only) */
+    int32_t splice;     /* GCONN_SPLICE_* (Union-Rem-CAS / Union-Rem-Lock only) */
     int32_t lt_rules;   /* GCONN_LT_* bits (Liu-Tarjan only) */
     int32_t block;      /* threads per block, 0 = library default */
     uint64_t seed;      /* L_max / BFS-source sampling and Union-JTB priorities */

@@ -168,6 +168,91 @@ def union_rem_cas(u, v, P, compress, splice):
     return None
 
 
+def union_rem_lock(u, v, P, compress, splice, locks):
+    """Algorithm 10 (Rem's algorithm with a lock per root).  Reading: after
+    the lock is taken, r_u is linked only if it is still a root above P[r_v];
+    otherwise the loop continues (one thread: the lock is always free)."""
+    ru, rv = u, v
+    while P[ru] != P[rv]:
+        if P[ru] < P[rv]:
+            ru, rv = rv, ru
+        if ru == P[ru]:
+            locks[ru] = 1
+            pv = P[rv]
+            linked = ru == P[ru] and ru > pv
+            if linked:
+                P[ru] = pv
+            locks[ru] = 0
+            if linked:
+                if compress is not find_naive:
+                    compress(u, P)
+                    compress(v, P)
+                return ru
+        else:
+            ru = splice(ru, rv, P)
+    return None
+
+
+def union_afforest(u, v, P):
+    """The finish rule of Afforest (Sutton, Ben-Nun, Bar-Noy 2018): compare the
+    parents, hook the higher one onto the lower when it is a root, otherwise
+    climb the higher side by two levels and the lower by one."""
+    p1, p2 = P[u], P[v]
+    while p1 != p2:
+        high, low = max(p1, p2), min(p1, p2)
+        ph = P[high]
+        if ph == low:
+            return None
+        if ph == high and cas(P, high, high, low):
+            return high
+        p1, p2 = P[P[high]], P[low]
+    return None
+
+
+def label_propagation(n, edges, labels=None):
+    """Label Propagation (Section 3.4): every round the larger label of each
+    edge takes the smaller one, until a round changes nothing."""
+    lab = list(range(n)) if labels is None else list(labels)
+    rounds = 0
+    changed = True
+    while changed:
+        changed = False
+        rounds += 1
+        for (u, v) in edges:
+            lo = min(lab[u], lab[v])
+            if lab[u] > lo:
+                lab[u] = lo
+                changed = True
+            if lab[v] > lo:
+                lab[v] = lo
+                changed = True
+    return lab, rounds
+
+
+def stergiou(n, edges, labels=None):
+    """Stergiou's algorithm as described in Section 3.4: like a Liu-Tarjan
+    ParentConnect round but with two label arrays -- messages are computed
+    from the previous round's array and applied to the current one -- then
+    one shortcut; until a round changes nothing."""
+    prev = list(range(n)) if labels is None else list(labels)
+    rounds = 0
+    while True:
+        rounds += 1
+        cur = list(prev)
+        for (u, v) in edges:
+            pu, pv = prev[u], prev[v]
+            if pv < cur[pu]:
+                cur[pu] = pv
+            if pu < cur[pv]:
+                cur[pv] = pu
+        cur = [cur[cur[x]] for x in range(n)]
+        if cur == prev:
+            break
+        prev = cur
+    full_shortcut(prev)
+    return prev, rounds
+
+
 def jtb_priority(v, seed):
     """Random priority of a vertex for Union-JTB tie-breaking (SplitMix64 finaliser)."""
     z = (seed * 0x9E3779B97F4A7C15 + v + 1) & 0xFFFFFFFFFFFFFFFF
@@ -248,8 +333,15 @@ class UF:
         self.H = [INF] * n
         self.W = [(0, v) for v in range(n)] if link == "jtb" else None
         self.two_try = find == "twotrysplit"
+        self.locks = [0] * n
 
     def union(self, u, v):
+        if self.link == "remlock":
+            return union_rem_lock(u, v, self.P, self.find, self.splice, self.locks)
+        if self.link == "afforest":
+            return union_afforest(u, v, self.P)
+        if self.link == "eclcc":
+            return union_async(u, v, self.P, find_split)
         if self.link == "async":
             return union_async(u, v, self.P, self.find)
         if self.link == "hooks":

@@ -30,7 +30,8 @@ GCONN_NOALLOC_MAX_N = 1 << 20
 # variant enums
 GCONN_SAMPLE_NONE, GCONN_SAMPLE_KOUT, GCONN_SAMPLE_HB, GCONN_SAMPLE_BFS = 0, 1, 2, 3
 (GCONN_LINK_ASYNC, GCONN_LINK_HOOKS, GCONN_LINK_EARLY, GCONN_LINK_REMCAS, GCONN_LINK_JTB,
- GCONN_LINK_SV, GCONN_LINK_LT) = range(7)
+ GCONN_LINK_SV, GCONN_LINK_LT, GCONN_LINK_REMLOCK, GCONN_LINK_ECLCC, GCONN_LINK_AFFOREST, GCONN_LINK_LP,
+ GCONN_LINK_STERGIOU) = range(12)
 (GCONN_FIND_NAIVE, GCONN_FIND_COMPRESS, GCONN_FIND_SPLIT, GCONN_FIND_HALVE, GCONN_FIND_TWOTRYSPLIT,
  GCONN_FIND_FULLSHORTCUT) = range(6)
 GCONN_SPLICE_NONE, GCONN_SPLICE_SPLIT_ONE, GCONN_SPLICE_HALVE_ONE, GCONN_SPLICE_SPLICE = 0, 1, 2, 3
@@ -38,7 +39,8 @@ GCONN_LT_CONNECT, GCONN_LT_PARENT, GCONN_LT_EXTENDED = 0, 1, 2
 GCONN_LT_ROOTUPDATE, GCONN_LT_FULLSHORTCUT, GCONN_LT_ALTER = 4, 8, 16
 
 SAMPLES = {"none": 0, "kout": 1, "hb": 2, "bfs": 3}
-LINKS = {"async": 0, "hooks": 1, "early": 2, "remcas": 3, "jtb": 4, "sv": 5, "lt": 6}
+LINKS = {"async": 0, "hooks": 1, "early": 2, "remcas": 3, "jtb": 4, "sv": 5, "lt": 6, "remlock": 7,
+         "eclcc": 8, "afforest": 9, "lp": 10, "stergiou": 11}
 FINDS = {"naive": 0, "compress": 1, "split": 2, "halve": 3, "twotrysplit": 4, "fullshortcut": 5}
 SPLICES = {"none": 0, "split_one": 1, "halve_one": 2, "splice": 3}
 

@@ -333,13 +333,19 @@ extern "C" gconn_status gconn_variant_check(const gconn_variant* v, int input_ki
     if (want_forest < 0 || want_forest > 2) return GCONN_E_INVAL;
     if (v->reserved != 0) return GCONN_E_INVAL;
     if (v->sample < 0 || v->sample > GCONN_SAMPLE_BFS) return GCONN_E_INVAL;
-    if (v->link < 0 || v->link > GCONN_LINK_LT) return GCONN_E_INVAL;
+    if (v->link < 0 || v->link > GCONN_LINK_STERGIOU) return GCONN_E_INVAL;
     if (v->find < 0 || v->find > GCONN_FIND_FULLSHORTCUT) return GCONN_E_INVAL;
     if (v->splice < 0 || v->splice > GCONN_SPLICE_SPLICE) return GCONN_E_INVAL;
     if (v->k < 0 || v->hb_n < 0 || v->k > 1024 || v->hb_n > 1024) return GCONN_E_INVAL;
     if (v->block != 0 && (v->block < 64 || v->block > 1024 || v->block % 32 != 0)) return GCONN_E_INVAL;
     if (v->sample != GCONN_SAMPLE_NONE && input_kind == 0) return GCONN_E_UNSUPPORTED;
-    bool rem = v->link == GCONN_LINK_REMCAS, jtb = v->link == GCONN_LINK_JTB;
+    bool rem = v->link == GCONN_LINK_REMCAS || v->link == GCONN_LINK_REMLOCK, jtb = v->link == GCONN_LINK_JTB;
+    bool fixed_find = v->link == GCONN_LINK_SV || v->link == GCONN_LINK_ECLCC || v->link == GCONN_LINK_AFFOREST ||
+                      v->link == GCONN_LINK_LP || v->link == GCONN_LINK_STERGIOU;
+    if (fixed_find && v->find != GCONN_FIND_NAIVE && v->find != GCONN_FIND_FULLSHORTCUT)
+        return GCONN_E_UNSUPPORTED;
+    // LP and Stergiou move non-roots between trees: components only
+    if ((v->link == GCONN_LINK_LP || v->link == GCONN_LINK_STERGIOU) && want_forest) return GCONN_E_UNSUPPORTED;
     if (v->splice != GCONN_SPLICE_NONE && !rem) return GCONN_E_UNSUPPORTED;
     if (v->find == GCONN_FIND_TWOTRYSPLIT && !jtb) return GCONN_E_UNSUPPORTED;
     if (rem && v->find == GCONN_FIND_COMPRESS) return GCONN_E_UNSUPPORTED;
@@ -349,8 +355,6 @@ extern "C" gconn_status gconn_variant_check(const gconn_variant* v, int input_ki
         return GCONN_E_UNSUPPORTED;
     if (jtb && v->find != GCONN_FIND_NAIVE && v->find != GCONN_FIND_TWOTRYSPLIT &&
         v->find != GCONN_FIND_FULLSHORTCUT)
-        return GCONN_E_UNSUPPORTED;
-    if (v->link == GCONN_LINK_SV && v->find != GCONN_FIND_NAIVE && v->find != GCONN_FIND_FULLSHORTCUT)
         return GCONN_E_UNSUPPORTED;
     if (v->link == GCONN_LINK_LT) {
         if (!lt_valid(v->lt_rules)) return GCONN_E_UNSUPPORTED;

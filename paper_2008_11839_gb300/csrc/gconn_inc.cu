@@ -19,6 +19,7 @@ struct gconn_inc {
     uint32_t* P;
     uint32_t* H;
     u64w* W;
+    uint32_t* Lk;
     cudaStream_t last;
 };
 
@@ -76,7 +77,11 @@ static gconn_status query_dispatch(const Variant& v, const UFState& s, const uin
     }
 }
 
-static UFState handle_state(gconn_inc* h) { return make_state(h->n, h->P, h->H, h->W, nullptr, h->v); }
+static UFState handle_state(gconn_inc* h) {
+    UFState s = make_state(h->n, h->P, h->H, h->W, nullptr, h->v);
+    s.Lk = h->Lk;
+    return s;
+}
 
 bool inc_view(const gconn_inc* h, IncView* out) {
     if (!h || !out) return false;
@@ -110,6 +115,10 @@ extern "C" gconn_status gconn_inc_create(uint32_t n, const gconn_variant* vin, v
     cudaError_t e = cudaMalloc(&h->P, sizeof(uint32_t) * cnt);
     if (e == cudaSuccess && v.link == GCONN_LINK_HOOKS) e = cudaMalloc(&h->H, sizeof(uint32_t) * cnt);
     if (e == cudaSuccess && v.link == GCONN_LINK_JTB) e = cudaMalloc(&h->W, sizeof(u64w) * cnt);
+    if (e == cudaSuccess && v.link == GCONN_LINK_REMLOCK) {
+        e = cudaMalloc(&h->Lk, sizeof(uint32_t) * cnt);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->Lk, 0, sizeof(uint32_t) * cnt, st);
+    }
     if (e != cudaSuccess) {
         gconn_inc_destroy(h);
         return cuda_status(e);
@@ -134,7 +143,7 @@ extern "C" gconn_status gconn_inc_insert_batch(gconn_inc* h, uint64_t b, const u
     bool host = !is_device_ptr(edges);
     GC_TRY(stage_in(edges, sizeof(uint32_t) * 2 * b, st, eb, (const void**)&de));
     UFState s = handle_state(h);
-    if (h->v.link == GCONN_LINK_SV || h->v.link == GCONN_LINK_LT) {
+    if (is_rounds_link(h->v.link)) {
         GC_TRY(rounds_coo(h->v, s, de, nullptr, b, st));
     } else {
         GC_TRY(union_coo(h->v, s, de, b, 0, st));
@@ -196,6 +205,7 @@ extern "C" gconn_status gconn_inc_destroy(gconn_inc* h) {
     if (h->P) cudaFree(h->P);
     if (h->H) cudaFree(h->H);
     if (h->W) cudaFree(h->W);
+    if (h->Lk) cudaFree(h->Lk);
     cudaSetDevice(prev);
     delete h;
     return GCONN_OK;

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "gc_internal.h"
+#include "gc_static.h"
 
 using namespace gc;
 
@@ -57,7 +58,7 @@ gconn_status capture_plan(Body&& body, gconn_plan** out) {
 gconn_status plan_variant_ok(const gconn_variant* vin, int input_kind) {
     Variant v;
     GC_TRY(resolve_variant(vin, input_kind, 0, &v));
-    if (v.sample == GCONN_SAMPLE_BFS || v.link == GCONN_LINK_SV || v.link == GCONN_LINK_LT)
+    if (v.sample == GCONN_SAMPLE_BFS || is_rounds_link(v.link))
         return GCONN_E_UNSUPPORTED;   // these read a device flag on the host every round
     return GCONN_OK;
 }

@@ -171,6 +171,49 @@ __global__ void k_lt_alter(uint2* E, uint64_t m, const uint32_t* P, uint32_t* ch
     if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicOr(changed, 1u);
 }
 
+// --------------------------------------------------------------------- LP
+// Label Propagation round: the larger label of each edge takes the smaller.
+__global__ void __launch_bounds__(256) k_lp(const uint2* __restrict__ E, uint64_t m, uint32_t n, uint32_t* P,
+                                            uint32_t* changed, uint32_t* err) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    bool ch = false;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        uint2 e = E[i];
+        if (e.x >= n || e.y >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
+        uint32_t a = __ldcg(P + e.x), b = __ldcg(P + e.y);
+        if (a == b) continue;
+        uint32_t lo = min(a, b);
+        if (a > lo) atomicMin(P + e.x, lo);
+        if (b > lo) atomicMin(P + e.y, lo);
+        ch = true;
+    }
+    if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicOr(changed, 1u);
+}
+
+// ---------------------------------------------------------------- Stergiou
+// One round over the previous labels: the entry of each endpoint's label
+// receives the other endpoint's label (atomicMin into the current array).
+__global__ void __launch_bounds__(256) k_stergiou(const uint2* __restrict__ E, uint64_t m, uint32_t n,
+                                                  const uint32_t* prev, uint32_t* P, uint32_t* err) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        uint2 e = E[i];
+        if (e.x >= n || e.y >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
+        uint32_t a = prev[e.x], b = prev[e.y];
+        if (a == b) continue;
+        if (b < a) atomicMin(P + a, b);
+        else atomicMin(P + b, a);
+    }
+}
+
+// Compare the current labels with the previous ones (a change means another round).
+__global__ void k_changed(uint32_t n, const uint32_t* prev, const uint32_t* P, uint32_t* changed) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    bool ch = false;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) ch |= prev[x] != P[x];
+    if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicOr(changed, 1u);
+}
+
 // ------------------------------------------------------------- CSR gather
 struct Gather {
     uint2* E;
@@ -344,10 +387,54 @@ static gconn_status run_lt(const Variant& v, const UFState& s, const uint2* E_in
     return compress_all(va, s, st);
 }
 
+static gconn_status run_lp(const Variant& v, const UFState& s, const uint2* E, uint64_t m, cudaStream_t st) {
+    RoundFlag flag;
+    GC_TRY(flag.init(st));
+    for (uint32_t round = 0; m; ++round) {
+        if (round >= MAX_ROUNDS) return GCONN_E_NONCONVERGED;
+        GC_TRY(flag.reset(st));
+        GC_TRY(launch("lp", k_lp, grid_for(k_lp, 256, m), 256, 0, st, E, m, s.n, s.P, flag.d(), s.err));
+        bool changed = false;
+        GC_TRY(flag.read(st, &changed));
+        if (!changed) break;
+    }
+    Variant va = v;
+    va.link = GCONN_LINK_ASYNC;
+    return compress_all(va, s, st);
+}
+
+static gconn_status run_stergiou(const Variant& v, const UFState& s, const uint2* E, uint64_t m, cudaStream_t st) {
+    uint32_t n = s.n;
+    DevBuf prevb;
+    GC_TRY(prevb.alloc(sizeof(uint32_t) * (size_t)n, st));
+    uint32_t* prev = prevb.as<uint32_t>();
+    RoundFlag flag;
+    GC_TRY(flag.init(st));
+    unsigned gn = grid_for(k_copy_u32, 256, n);
+    for (uint32_t round = 0; m; ++round) {
+        if (round >= MAX_ROUNDS) return GCONN_E_NONCONVERGED;
+        GC_TRY(flag.reset(st));
+        GC_TRY(launch("stergiou_copy", k_copy_u32, gn, 256, 0, st, n, (const uint32_t*)s.P, prev));
+        GC_TRY(launch("stergiou", k_stergiou, grid_for(k_stergiou, 256, m), 256, 0, st, E, m, n,
+                      (const uint32_t*)prev, s.P, s.err));
+        GC_TRY(launch("lt_shortcut", k_lt_shortcut, gn, 256, 0, st, n, s.P, flag.d()));
+        GC_TRY(launch("stergiou_changed", k_changed, gn, 256, 0, st, n, (const uint32_t*)prev,
+                      (const uint32_t*)s.P, flag.d()));
+        bool changed = false;
+        GC_TRY(flag.read(st, &changed));
+        if (!changed) break;
+    }
+    Variant va = v;
+    va.link = GCONN_LINK_ASYNC;
+    return compress_all(va, s, st);
+}
+
 gconn_status rounds_coo(const Variant& v, const UFState& s, const uint32_t* edges, const uint32_t* eids, uint64_t m,
                         cudaStream_t st) {
     if (s.n == 0) return GCONN_OK;
     if (v.link == GCONN_LINK_SV) return run_sv(v, s, (const uint2*)edges, eids, m, st);
+    if (v.link == GCONN_LINK_LP) return run_lp(v, s, (const uint2*)edges, m, st);
+    if (v.link == GCONN_LINK_STERGIOU) return run_stergiou(v, s, (const uint2*)edges, m, st);
     return run_lt(v, s, (const uint2*)edges, eids, m, st);
 }
 

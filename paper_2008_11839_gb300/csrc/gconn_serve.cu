@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(256) k_serve(const uint2* __restrict__ pairs, 
         }
         const Seg& g = segs[lo];
         UFState s;
-        s.P = g.P; s.H = g.H; s.W = g.W; s.sf = nullptr; s.err = err; s.n = g.n; s.cap = g.cap; s.seed = g.seed;
+        s.P = g.P; s.H = g.H; s.W = g.W; s.sf = nullptr; s.err = err; s.Lk = nullptr;
+        s.n = g.n; s.cap = g.cap; s.seed = g.seed;
         uint2 e = __ldcs(pairs + i);
         bool inrange = e.x < g.n && e.y < g.n;
         if (!inrange) atomicOr(err, GC_DERR_RANGE);
@@ -494,7 +495,11 @@ extern "C" gconn_status gconn_server_open_session(gconn_server* S, uint32_t n, c
     ses.id = id;
     ses.h = h;
     inc_view(h, &ses.view);
-    ses.mergeable = ses.view.v.link != GCONN_LINK_SV && ses.view.v.link != GCONN_LINK_LT;
+    {
+        int l = ses.view.v.link;   // rules the merged kernel is instantiated for
+        ses.mergeable = l == GCONN_LINK_ASYNC || l == GCONN_LINK_HOOKS || l == GCONN_LINK_EARLY ||
+                        l == GCONN_LINK_REMCAS || l == GCONN_LINK_JTB || l == GCONN_LINK_ECLCC;
+    }
     *session = id;
     return GCONN_OK;
 }

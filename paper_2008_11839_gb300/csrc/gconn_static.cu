@@ -40,6 +40,16 @@ gconn_status dispatch_uf(int L, int F, int S, bool SF, Fn&& fn) {
     GC_UF_CASE(LK_REMCAS, FD_HALVE, SP_SPLICE)
     GC_UF_CASE(LK_JTB, FD_NAIVE, SP_NONE)
     GC_UF_CASE(LK_JTB, FD_TWOTRY, SP_NONE)
+    GC_UF_CASE(LK_REMLOCK, FD_NAIVE, SP_SPLIT_ONE)
+    GC_UF_CASE(LK_REMLOCK, FD_NAIVE, SP_HALVE_ONE)
+    GC_UF_CASE(LK_REMLOCK, FD_NAIVE, SP_SPLICE)
+    GC_UF_CASE(LK_REMLOCK, FD_SPLIT, SP_SPLIT_ONE)
+    GC_UF_CASE(LK_REMLOCK, FD_SPLIT, SP_HALVE_ONE)
+    GC_UF_CASE(LK_REMLOCK, FD_SPLIT, SP_SPLICE)
+    GC_UF_CASE(LK_REMLOCK, FD_HALVE, SP_SPLIT_ONE)
+    GC_UF_CASE(LK_REMLOCK, FD_HALVE, SP_HALVE_ONE)
+    GC_UF_CASE(LK_REMLOCK, FD_HALVE, SP_SPLICE)
+    GC_UF_CASE(LK_AFFOREST, FD_NAIVE, SP_NONE)
 #undef GC_UF_CASE
     return GCONN_E_UNSUPPORTED;
 }
@@ -48,13 +58,17 @@ gconn_status dispatch_uf(int L, int F, int S, bool SF, Fn&& fn) {
 void uf_triple(const Variant& v, int* L, int* F, int* S) {
     *L = v.link;
     int f = v.find;
+    if (v.link == GCONN_LINK_ECLCC) {   // ECL-CC's finish: Union-Async with path splitting
+        *L = LK_ASYNC;
+        f = GCONN_FIND_SPLIT;
+    }
     if (f == GCONN_FIND_FULLSHORTCUT) f = GCONN_FIND_NAIVE;
     *F = f == GCONN_FIND_COMPRESS ? FD_COMPRESS
        : f == GCONN_FIND_SPLIT ? FD_SPLIT
        : f == GCONN_FIND_HALVE ? FD_HALVE
        : f == GCONN_FIND_TWOTRYSPLIT ? FD_TWOTRY : FD_NAIVE;
     *S = SP_NONE;
-    if (v.link == GCONN_LINK_REMCAS)
+    if (v.link == GCONN_LINK_REMCAS || v.link == GCONN_LINK_REMLOCK)
         *S = v.splice == GCONN_SPLICE_SPLIT_ONE ? SP_SPLIT_ONE
            : v.splice == GCONN_SPLICE_HALVE_ONE ? SP_HALVE_ONE : SP_SPLICE;
 }
@@ -64,6 +78,7 @@ static int block_of(const Variant& v) { return v.block > 0 ? v.block : 256; }
 UFState make_state(uint32_t n, uint32_t* P, uint32_t* H, u64w* W, uint32_t* sf, const Variant& v) {
     UFState s;
     s.P = P; s.H = H; s.W = W; s.sf = sf;
+    s.Lk = nullptr;
     s.err = err_word();
     s.n = n;
     s.cap = v.cap;
@@ -187,7 +202,7 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
     uint32_t* lmax = nullptr;
     // the rounds-based finishes (SV, LT) sample with Union-Async
     Variant sv = v;
-    bool rounds = v.link == GCONN_LINK_SV || v.link == GCONN_LINK_LT;
+    bool rounds = is_rounds_link(v.link);
     if (rounds) { sv.link = GCONN_LINK_ASYNC; sv.find = GCONN_FIND_NAIVE; sv.splice = 0; }
     if (sampled) {
         GC_TRY(sc.lmax.alloc(sizeof(uint32_t), st));
@@ -319,8 +334,14 @@ static gconn_status static_run(uint32_t n, uint64_t m, const uint32_t* edges, co
     if (v.link == GCONN_LINK_HOOKS) { GC_TRY(hbuf.alloc(sizeof(uint32_t) * (size_t)n, st)); H = hbuf.as<uint32_t>(); }
     if (v.link == GCONN_LINK_JTB) { GC_TRY(wbuf.alloc(sizeof(u64w) * (size_t)n, st)); W = wbuf.as<u64w>(); }
     if (want_forest) { GC_TRY(sfbuf.alloc(sizeof(uint32_t) * (size_t)n, st)); sf = sfbuf.as<uint32_t>(); }
+    DevBuf lkbuf;
 
     UFState s = make_state(n, P, H, W, sf, v);
+    if (v.link == GCONN_LINK_REMLOCK) {
+        GC_TRY(lkbuf.alloc(sizeof(uint32_t) * (size_t)n, st));
+        s.Lk = lkbuf.as<uint32_t>();
+        GC_CUDA(cudaMemsetAsync(s.Lk, 0, sizeof(uint32_t) * (size_t)n, st));
+    }
     L2Window l2win;
     l2win.apply(st, P, sizeof(uint32_t) * (size_t)n);
     GC_TRY(init_state(s, st));
@@ -328,7 +349,7 @@ static gconn_status static_run(uint32_t n, uint64_t m, const uint32_t* edges, co
         GC_TRY(launch("check_arcs", k_check_arcs, 1, 1, 0, st, d_off, n, s.err));
 
     if (!csr) {
-        if (v.link == GCONN_LINK_SV || v.link == GCONN_LINK_LT) {
+        if (is_rounds_link(v.link)) {
             GC_TRY(rounds_coo(v, s, d_edges, nullptr, m, st));
         } else {
             GC_TRY(union_coo(v, s, d_edges, m, 0, st));

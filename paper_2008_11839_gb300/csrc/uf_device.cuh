@@ -18,7 +18,7 @@
 
 namespace gc {
 
-enum { LK_ASYNC = 0, LK_HOOKS = 1, LK_EARLY = 2, LK_REMCAS = 3, LK_JTB = 4 };
+enum { LK_ASYNC = 0, LK_HOOKS = 1, LK_EARLY = 2, LK_REMCAS = 3, LK_JTB = 4, LK_REMLOCK = 7, LK_AFFOREST = 9 };
 enum { FD_NAIVE = 0, FD_COMPRESS = 1, FD_SPLIT = 2, FD_HALVE = 3, FD_TWOTRY = 4 };
 enum { SP_NONE = 0, SP_SPLIT_ONE = 1, SP_HALVE_ONE = 2, SP_SPLICE = 3 };
 
@@ -35,6 +35,7 @@ struct UFState {
     u64w* W;          // (rank << 32) | parent words (Union-JTB)
     uint32_t* sf;     // spanning-forest slot per vertex (edge / arc id), INF = none
     uint32_t* err;    // device error word
+    uint32_t* Lk;     // per-vertex locks, 0 = free (Union-Rem-Lock)
     uint32_t n;
     uint32_t cap;     // per-operation loop cap
     uint32_t seed;    // Union-JTB priority seed
@@ -255,6 +256,92 @@ __device__ __forceinline__ bool union_remcas(const UFState& s, uint32_t u, uint3
     }
 }
 
+// Union-Rem-Lock (Algorithm 10): Rem's climb, but a root is linked under a
+// lock on it (a plain store while holding the lock) instead of by CAS.  A
+// thread holds at most one lock and never waits for another lock while
+// holding it, so lock waits always end; each wait is one bounded Spin step.
+// After taking the lock, r_u is linked only if it is still a root above the
+// current P[r_v]; otherwise the climb continues from the fresh values.
+template <int F, int S, bool SF>
+__device__ __forceinline__ bool union_remlock(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
+    uint32_t* P = s.P;
+    uint32_t ru = u, rv = v;
+    uint32_t pu = ldq<true>(P, ru), pv = ldq<true>(P, rv);
+    while (true) {
+        if (pu == pv) return false;
+        if (pu < pv) {
+            uint32_t t = ru; ru = rv; rv = t;
+            t = pu; pu = pv; pv = t;
+        }
+        if (ru == pu) {
+            if (atomicCAS(s.Lk + ru, 0u, 1u) == 0u) {
+                uint32_t cur = ldp(P, ru), pvf = ldp(P, rv);
+                bool linked = cur == ru && ru > pvf;
+                if (linked) {
+                    stp(P, ru, pvf);
+                    if (SF) s.sf[ru] = eid;
+                }
+                __threadfence();
+                atomicExch(s.Lk + ru, 0u);
+                if (linked) {
+                    if (F != FD_NAIVE) {
+                        uf_find<F, true>(s, u, sp);
+                        uf_find<F, true>(s, v, sp);
+                    }
+                    return true;
+                }
+                pu = cur;
+                pv = pvf;
+            } else {                        // lock held by another thread: re-read
+                pu = ldp(P, ru);
+                pv = ldp(P, rv);
+            }
+        } else if (S == SP_SPLICE) {
+            atomicCAS(P + ru, pu, pv);
+            ru = pu;
+            pu = ldq<true>(P, ru);
+        } else {
+            uint32_t w = ldq<true>(P, pu);
+            if (w != pu) atomicCAS(P + ru, pu, w);
+            if (S == SP_SPLIT_ONE) {
+                ru = pu;
+                pu = w;
+            } else {
+                ru = w;
+                pu = ldq<true>(P, w);
+            }
+        }
+        if (!sp.step(s)) return false;
+    }
+}
+
+// The finish rule of Afforest (Sutton, Ben-Nun, Bar-Noy, IPDPS 2018):
+// compare the two parents; if the higher one's parent is the lower one they
+// are joined; if the higher one is a root, CAS it onto the lower one; else
+// climb the higher side two levels and the lower side one.
+template <bool SF>
+__device__ __forceinline__ bool union_afforest(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
+    uint32_t* P = s.P;
+    uint32_t p1 = ldq<true>(P, u), p2 = ldq<true>(P, v);
+    while (p1 != p2) {
+        uint32_t high = p1 > p2 ? p1 : p2, low = p1 > p2 ? p2 : p1;
+        uint32_t ph = ldq<true>(P, high);
+        if (ph == low) return false;
+        if (ph == high) {
+            uint32_t old = atomicCAS(P + high, high, low);
+            if (old == high) {
+                if (SF) s.sf[high] = eid;
+                return true;
+            }
+            ph = old;
+        }
+        p1 = ldq<true>(P, ph);
+        p2 = ldq<true>(P, low);
+        if (!sp.step(s)) return false;
+    }
+    return false;
+}
+
 // ----------------------------------------------------------- Union-JTB
 // Randomized linking by rank on 64-bit (rank, parent) words: the root with
 // the smaller key (rank, priority, id) is linked under the other; on equal
@@ -341,6 +428,8 @@ __device__ __forceinline__ bool uf_union(const UFState& s, uint32_t u, uint32_t 
     if (L == LK_HOOKS) return union_hooks<F, SF>(s, u, v, eid, sp);
     if (L == LK_EARLY) return union_early<F, SF>(s, u, v, eid, sp);
     if (L == LK_REMCAS) return union_remcas<F, S, SF>(s, u, v, eid, sp);
+    if (L == LK_REMLOCK) return union_remlock<F, S, SF>(s, u, v, eid, sp);
+    if (L == LK_AFFOREST) return union_afforest<SF>(s, u, v, eid, sp);
     return union_jtb<F, SF>(s, u, v, eid, sp);
 }
 

@@ -12,13 +12,17 @@ for _f in ["naive", "split", "halve"]:
     for _s in ["split_one", "halve_one", "splice"]:
         UF_COMBOS.append(("remcas", _f, _s))
 UF_COMBOS += [("jtb", "naive", "none"), ("jtb", "twotrysplit", "none")]
+for _f in ["naive", "split", "halve"]:
+    for _s in ["split_one", "halve_one", "splice"]:
+        UF_COMBOS.append(("remlock", _f, _s))
+UF_COMBOS += [("afforest", "naive", "none"), ("eclcc", "naive", "none")]
 
 LT_ALL = ["CUSA", "CRSA", "PUSA", "PRSA", "PUS", "PRS", "EUSA", "EUS",
           "CUFA", "CRFA", "PUFA", "PRFA", "PUF", "PRF", "EUFA", "EUF"]
 LT_ROOT = ["CRSA", "PRSA", "PRS", "CRFA", "PRFA", "PRF"]
 
 
-UF_FOREST = [c for c in UF_COMBOS if not (c[0] == "remcas" and c[2] == "splice")]
+UF_FOREST = [c for c in UF_COMBOS if not (c[0] in ("remcas", "remlock") and c[2] == "splice")]
 
 
 def combo_id(c):

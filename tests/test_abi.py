@@ -87,6 +87,16 @@ def test_all_valid_uf_combinations_accepted(lib):
             assert g.gconn_variant_check(v, 0, 1) == want        # forest: splice is not root-based
     for f in ["naive", "twotrysplit"]:
         assert g.gconn_variant_check(g.make_variant(link="jtb", find=f), 1, 1) == 0
+    for sp in ["split_one", "halve_one"]:
+        assert g.gconn_variant_check(g.make_variant(link="remlock", find="halve", splice=sp), 0, 1) == 0
+    assert g.gconn_variant_check(g.make_variant(link="remlock", splice="splice"), 0, 1) == b.GCONN_E_UNSUPPORTED
+    for link in ["afforest", "eclcc"]:
+        assert g.gconn_variant_check(g.make_variant(link=link), 0, 1) == 0
+        assert g.gconn_variant_check(g.make_variant(link=link, find="halve"), 0, 0) == b.GCONN_E_UNSUPPORTED
+    for link in ["lp", "stergiou"]:
+        assert g.gconn_variant_check(g.make_variant(link=link), 1, 0) == 0
+        assert g.gconn_variant_check(g.make_variant(link=link), 0, 1) == b.GCONN_E_UNSUPPORTED
+        assert g.gconn_variant_check(g.make_variant(link=link), 0, 2) == b.GCONN_E_UNSUPPORTED
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

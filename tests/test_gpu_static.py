@@ -103,6 +103,23 @@ def test_liu_tarjan(rules):
             assert (_cc_csr(n, off, cols, v) == REF[name]).all(), (name, rules, sample)
 
 
+@pytest.mark.parametrize("link", ["lp", "stergiou"])
+def test_label_propagation_and_stergiou(link):
+    for sample in ["none", "kout"]:
+        v = g.make_variant(sample=sample, link=link)
+        for name, n, e in GRAPHS:
+            if sample == "none":
+                assert (_cc_coo(n, e, v) == REF[name]).all(), (name, link)
+            off, cols = CSR[name]
+            assert (_cc_csr(n, off, cols, v) == REF[name]).all(), (name, link, sample)
+    import torch
+    f = torch.empty(4, dtype=torch.int64, device="cuda")
+    c = torch.empty(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(g.GconnError) as ex:          # not root-based: no forest
+        g.gconn_spanning_forest(3, 1, dev(np.array([[0, 1]], np.uint32)), f, c, None, g.make_variant(link=link))
+    assert ex.value.status == g.GCONN_E_UNSUPPORTED
+
+
 @pytest.mark.parametrize("rules", LT_ROOT)
 def test_liu_tarjan_forest(rules):
     v = g.make_variant(link="lt", lt=rules)

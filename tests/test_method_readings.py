@@ -36,6 +36,10 @@ for f in ["naive", "split", "halve"]:
     for sp in ["split_one", "halve_one", "splice"]:
         COMBOS.append(("remcas", f, sp))
 COMBOS += [("jtb", "naive", "splice"), ("jtb", "twotrysplit", "splice")]
+for f in ["naive", "split", "halve"]:
+    for sp in ["split_one", "halve_one", "splice"]:
+        COMBOS.append(("remlock", f, sp))
+COMBOS += [("afforest", "naive", "splice"), ("eclcc", "naive", "splice")]
 
 
 @pytest.mark.parametrize("sample", ["none", "kout", "hb", "bfs"])
@@ -124,3 +128,23 @@ def test_parent_connect_to_endpoints_stalls():
     assert newP == P                       # no progress: would end unmerged
     lab, _ = mr.liu_tarjan(n, edges, "PRS", labels=P)
     assert lab == [0, 0, 0, 0]
+
+
+def test_label_propagation_and_stergiou_readings():
+    for n, e in GRAPHS:
+        el = [tuple(x) for x in e.tolist()]
+        ref = oracle.cc_uf(n, e)
+        lab, _ = mr.label_propagation(n, el)
+        assert (np.array(lab, np.uint32) == ref).all()
+        lab, _ = mr.stergiou(n, el)
+        assert (np.array(lab, np.uint32) == ref).all()
+
+
+def test_label_propagation_rounds_track_diameter():
+    """LP needs about one round per hop of the longest shortest path: a path
+    of k vertices with ids increasing along it takes k rounds (Section 4.2
+    attributes LP's slowness on high-diameter graphs to this)."""
+    k = 40
+    path = [(i, i + 1) for i in reversed(range(k - 1))]   # far end first: one hop per round
+    lab, rounds = mr.label_propagation(k, path)
+    assert lab == [0] * k and rounds >= k - 1
