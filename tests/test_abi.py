@@ -70,7 +70,7 @@ def test_out_of_range_fields(lib):
     v = g.make_variant(block=100)
     assert g.gconn_variant_check(v, 0, 0) == b.GCONN_E_INVAL
     v = g.make_variant()
-    v.link = 9
+    v.link = 12
     assert g.gconn_variant_check(v, 0, 0) == b.GCONN_E_INVAL
 
 
