@@ -637,6 +637,26 @@ def run_sweep(args):
     print(json.dumps({"sweep_best": ok[:10], "all_exact": all(r["exact"] for r in ok), "variants": len(rows)}))
 
 
+def run_stats(args):
+    """Sampling quality on the RMAT s22 graph (the paper's Table 4 columns):
+    Cov, IC, Time % and arcs inspected, per sampling method."""
+    import torch
+    import paper_2008_11839_gb300 as g
+    g.build()
+    dev = torch.device("cuda", 0)
+    n, e, off, cols, seed = make_static_input(0, args.scale, args.edges)
+    d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+    d_cols = torch.from_numpy(cols.view(np.int32)).to(dev)
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    for spec in args.stats_variants.split(","):
+        v = parse_variant(g, spec)
+        for _ in range(2):                   # warm, then report the second run
+            st = g.gconn_cc_csr_stats(n, d_off, d_cols, lab, v)
+        d = st.as_dict()
+        d["variant"] = spec
+        print(json.dumps(d), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -658,6 +678,9 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="time every sampling x finish variant (RMAT s22)")
     ap.add_argument("--sweep-samples", default="none,kout,hb,bfs")
     ap.add_argument("--sweep-steps", type=int, default=5)
+    ap.add_argument("--stats", action="store_true", help="sampling Cov / IC / Time %% per sampling method")
+    ap.add_argument("--stats-variants", default="kout/remcas/naive/split_one,hb/remcas/naive/split_one,"
+                                                 "bfs/remcas/naive/split_one,none/remcas/naive/split_one")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -666,6 +689,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.sweep:
         run_sweep(args)
+        return
+    if args.stats:
+        run_stats(args)
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)

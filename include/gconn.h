@@ -142,6 +142,31 @@ gconn_status gconn_cc(uint32_t n, uint64_t m, const uint32_t* edges, uint32_t* l
 gconn_status gconn_cc_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
                           uint32_t* labels, const gconn_variant* v, void* stream);
 
+/* ---------------------------------------------- sampling instrumentation */
+/* The quantities of Section 4.3 (Table 4 and the edges-inspected figure) for
+ * one CSR run: after the sampling phase, Cov = lmax_vertices / n (vertices in
+ * the L_max component, whose arcs the finish skips), IC =
+ * inter_component_arcs / arcs (arcs whose endpoints have different sampled
+ * labels), Time % = sample_ms / total_ms, plus the arcs the sampling step
+ * inspected (k-out, HB; 0 for BFS and none) and the finish's active vertices
+ * and arcs.  The run is a separate counting pass (extra kernels, one host
+ * synchronisation), not the timed path.  Device buffers only; labels receives
+ * the canonical labels.  Union-JTB and the round-based finishes:
+ * GCONN_E_UNSUPPORTED. */
+typedef struct gconn_sample_stats {
+    uint64_t n, arcs;
+    uint64_t lmax_vertices;          /* Cov numerator */
+    uint64_t sampled_components;     /* roots after sampling */
+    uint64_t active_vertices;        /* label != L_max and degree > 0 */
+    uint64_t active_arcs;            /* arcs of the active vertices */
+    uint64_t inter_component_arcs;   /* IC numerator */
+    uint64_t sample_arcs_inspected;
+    uint64_t lmax;                   /* the chosen L_max (0xFFFFFFFF without sampling) */
+    double sample_ms, total_ms;      /* CUDA events around sampling and the pass */
+} gconn_sample_stats;
+gconn_status gconn_cc_csr_stats(uint32_t n, const uint64_t* offsets, const uint32_t* cols, uint32_t* labels,
+                                const gconn_variant* v, gconn_sample_stats* out, void* stream);
+
 /* ------------------------------------------------------ spanning forest */
 /* Spanning forest (Algorithm 2): every root that stops being a root records
  * the input edge that linked it (Section 3.2).  Output ids are COO edge

@@ -88,6 +88,20 @@ class gconn_server_config(ctypes.Structure):
                 ("reserved", ctypes.c_uint32)]
 
 
+class gconn_sample_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("n", "arcs", "lmax_vertices", "sampled_components",
+                                               "active_vertices", "active_arcs", "inter_component_arcs",
+                                               "sample_arcs_inspected", "lmax")] + \
+               [("sample_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["cov"] = self.lmax_vertices / max(self.n, 1)
+        d["ic"] = self.inter_component_arcs / max(self.arcs, 1)
+        d["time_pct"] = self.sample_ms / self.total_ms if self.total_ms else 0.0
+        return d
+
+
 class GconnError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -137,6 +151,8 @@ _SIGS = {
     "gconn_server_close_session": (_i32, [_vp, _u32]),
     "gconn_server_stats": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "gconn_server_destroy": (_i32, [_vp]),
+    "gconn_cc_csr_stats": (_i32, [_u32, _vp, _vp, _vp, ctypes.POINTER(gconn_variant),
+                                  ctypes.POINTER(gconn_sample_stats), _vp]),
     "gconn_sync": (_i32, [_vp]),
     "gconn_status_str": (ctypes.c_char_p, [_i32]),
     "gconn_launch_count": (_u64, []),
@@ -394,6 +410,13 @@ def gconn_server_stats(h):
 
 def gconn_server_destroy(h):
     check(lib().gconn_server_destroy(h), "gconn_server_destroy")
+
+
+def gconn_cc_csr_stats(n, offsets, cols, labels, variant=None, stream=None) -> gconn_sample_stats:
+    out = gconn_sample_stats()
+    check(lib().gconn_cc_csr_stats(n, ptr(offsets), ptr(cols), ptr(labels), _vref(variant), ctypes.byref(out),
+                                   stream_handle(stream)), "gconn_cc_csr_stats")
+    return out
 
 
 def gconn_sync(stream=None):

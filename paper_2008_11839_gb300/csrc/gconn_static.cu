@@ -193,8 +193,46 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off,
 
 // Runs the sampling phase (unless NONE), L_max, vertex gathering and the
 // finish phase of Algorithm 1 on CSR.  Leaves P (or W) final, not finalised.
+// Counters of the sampling phase for gconn_cc_csr_stats (Section 4.3, Table 4).
+struct CsrStats {
+    unsigned long long* d;        // device counters, see k_sample_stats
+    cudaEvent_t t_sampled;        // recorded after sampling + L_max
+    uint32_t* lmax;               // device scalar, copied out by the caller
+};
+
+// After sampling and compression (P[v] = sampled root): vertices labelled
+// L_max, sampled components (roots), active vertices and their arcs, arcs
+// whose endpoints carry different sampled labels, and arcs the sampling step
+// inspected.
+static __global__ void k_sample_stats(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols,
+                                      const uint32_t* P, uint32_t n, const uint32_t* lmax_p, int sample, int k,
+                                      int hb_n, unsigned long long* c) {
+    uint32_t lmax = lmax_p ? *lmax_p : GC_DINF;
+    unsigned long long cov = 0, roots = 0, act = 0, act_arcs = 0, inter = 0, insp = 0;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint32_t lv = P[v];
+        uint64_t lo = off[v], hi = off[v + 1], deg = hi - lo;
+        cov += lv == lmax;
+        roots += lv == (uint32_t)v;
+        if (lv != lmax && deg) {
+            act += 1;
+            act_arcs += deg;
+        }
+        for (uint64_t a = lo; a < hi; ++a) inter += P[cols[a]] != lv;
+        if (sample == GCONN_SAMPLE_KOUT) insp += deg < (uint64_t)k ? deg : (uint64_t)k;
+        if (sample == GCONN_SAMPLE_HB) insp += (deg > 0) + (lv == (uint32_t)v ? (deg < (uint64_t)hb_n ? deg : hb_n) : 0);
+    }
+    atomicAdd(c + 0, cov);
+    atomicAdd(c + 1, roots);
+    atomicAdd(c + 2, act);
+    atomicAdd(c + 3, act_arcs);
+    atomicAdd(c + 4, inter);
+    atomicAdd(c + 5, insp);
+}
+
 gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,
-                         cudaStream_t st) {
+                         cudaStream_t st, CsrStats* stats = nullptr) {
     uint32_t n = s.n;
     if (n == 0) return GCONN_OK;
     CsrScratch sc;
@@ -230,6 +268,13 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
         auto k = jtb ? k_vg<LK_JTB, true> : k_vg<LK_ASYNC, true>;
         GC_TRY(launch("vg", k, grid_for(k, 256, (uint64_t)n), 256, 0, st, off, s, lmax, active, small, cnt + 0,
                       tasks, (uint32_t)task_cap, cnt + 1, over, cnt + 2));
+    }
+    if (stats) {
+        GC_CUDA(cudaEventRecord(stats->t_sampled, st));
+        if (lmax) GC_CUDA(cudaMemcpyAsync(stats->lmax, lmax, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        if (!jtb)
+            GC_TRY(launch("sample_stats", k_sample_stats, grid_for(k_sample_stats, 256, n), 256, 0, st, off, cols,
+                          (const uint32_t*)s.P, n, (const uint32_t*)lmax, v.sample, v.k, v.hb_n, stats->d));
     }
     if (rounds) return rounds_csr(v, s, off, cols, active, small, cnt + 0, tasks, cnt + 1, (uint32_t)task_cap,
                                   over, cnt + 2, st);
@@ -383,6 +428,65 @@ extern "C" gconn_status gconn_cc_csr(uint32_t n, const uint64_t* offsets, const 
                                      const gconn_variant* v, void* stream) {
     if (!offsets) return GCONN_E_INVAL;
     return static_run(n, 0, nullptr, offsets, cols, labels, nullptr, nullptr, v, 0, stream);
+}
+
+extern "C" gconn_status gconn_cc_csr_stats(uint32_t n, const uint64_t* offsets, const uint32_t* cols, uint32_t* labels,
+                                           const gconn_variant* vin, gconn_sample_stats* out, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!out || !offsets || !labels || n == 0 || n == 0xFFFFFFFFu) return GCONN_E_INVAL;
+    if (!is_device_ptr(offsets) || !is_device_ptr(labels) || (cols && !is_device_ptr(cols))) return GCONN_E_INVAL;
+    Variant v;
+    GC_TRY(resolve_variant(vin, 1, 0, &v));
+    if (v.link == GCONN_LINK_JTB || is_rounds_link(v.link)) return GCONN_E_UNSUPPORTED;
+    memset(out, 0, sizeof(*out));
+    DevBuf cb, hbuf, lkbuf;
+    GC_TRY(cb.alloc(9 * sizeof(unsigned long long), st));
+    GC_CUDA(cudaMemsetAsync(cb.p, 0, 9 * sizeof(unsigned long long), st));
+    uint32_t* H = nullptr;
+    if (v.link == GCONN_LINK_HOOKS) { GC_TRY(hbuf.alloc(sizeof(uint32_t) * (size_t)n, st)); H = hbuf.as<uint32_t>(); }
+    UFState s = make_state(n, labels, H, nullptr, nullptr, v);
+    if (v.link == GCONN_LINK_REMLOCK) {
+        GC_TRY(lkbuf.alloc(sizeof(uint32_t) * (size_t)n, st));
+        s.Lk = lkbuf.as<uint32_t>();
+        GC_CUDA(cudaMemsetAsync(s.Lk, 0, sizeof(uint32_t) * (size_t)n, st));
+    }
+    cudaEvent_t e0, e1, e2;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    CsrStats cs{cb.as<unsigned long long>(), e1, (uint32_t*)(cb.as<unsigned long long>() + 8)};
+    GC_CUDA(cudaEventRecord(e0, st));
+    gconn_status r = init_state(s, st);
+    if (r == GCONN_OK) r = csr_connect(v, s, offsets, cols, st, &cs);
+    if (r == GCONN_OK) r = finalize_labels(v, s, labels, st);
+    if (r == GCONN_OK) r = cuda_status(cudaEventRecord(e2, st));
+    unsigned long long h[8] = {0};
+    if (r == GCONN_OK) r = cuda_status(cudaMemcpyAsync(h, cb.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    if (r == GCONN_OK) r = read_and_clear_err(st);
+    float ms_total = 0, ms_sample = 0;
+    if (r == GCONN_OK) {
+        cudaEventElapsedTime(&ms_sample, e0, e1);
+        cudaEventElapsedTime(&ms_total, e0, e2);
+        uint64_t narcs = 0;
+        cudaMemcpy(&narcs, offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost);
+        out->n = n;
+        out->arcs = narcs;
+        out->lmax_vertices = h[0];
+        out->sampled_components = h[1];
+        out->active_vertices = h[2];
+        out->active_arcs = h[3];
+        out->inter_component_arcs = h[4];
+        out->sample_arcs_inspected = h[5];
+        uint32_t lm = GC_DINF;
+        if (v.sample != GCONN_SAMPLE_NONE) cudaMemcpy(&lm, cs.lmax, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+        out->lmax = lm;
+        out->sample_ms = ms_sample;
+        out->total_ms = ms_total;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    return r;
 }
 
 extern "C" gconn_status gconn_spanning_forest(uint32_t n, uint64_t m, const uint32_t* edges, uint64_t* forest,

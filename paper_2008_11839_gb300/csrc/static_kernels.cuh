@@ -189,16 +189,16 @@ static __global__ void k_hb1(const uint64_t* __restrict__ off, const uint32_t* _
     }
 }
 
-// HB sampling step 2: every vertex that is still a root unions its first N
-// edges.
+// HB sampling step 2: every vertex that is still a root after step 1 unions
+// its first N edges.  "Still a root after step 1" is read from the row (no
+// smaller neighbour), not from P, which step-2 unions change concurrently.
 template <int L, int F, int S, bool SF>
 static __global__ void __launch_bounds__(256) k_hb2(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols,
                                              int N, UFState s) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
-        uint32_t p = (L == LK_JTB) ? wpar(ldw(s.W, (uint32_t)v)) : ldp(s.P, (uint32_t)v);
-        if (p != (uint32_t)v) continue;
         uint64_t lo = off[v], hi = off[v + 1];
+        if (hi > lo && cols[lo] < (uint32_t)v) continue;   // hooked in step 1
         uint64_t end = lo + (uint64_t)N < hi ? lo + (uint64_t)N : hi;
         for (uint64_t a = lo; a < end; ++a) {
             uint32_t w = cols[a];
