@@ -162,7 +162,8 @@ typedef struct gconn_sample_stats {
     uint64_t inter_component_arcs;   /* IC numerator */
     uint64_t sample_arcs_inspected;
     uint64_t lmax;                   /* the chosen L_max (0xFFFFFFFF without sampling) */
-    double sample_ms, total_ms;      /* CUDA events around sampling and the pass */
+    double sample_ms, total_ms;      /* CUDA events: init through sampling, L_max and gathering;
+                                        the whole pass without the counting kernel */
 } gconn_sample_stats;
 gconn_status gconn_cc_csr_stats(uint32_t n, const uint64_t* offsets, const uint32_t* cols, uint32_t* labels,
                                 const gconn_variant* v, gconn_sample_stats* out, void* stream);
