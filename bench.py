@@ -657,6 +657,49 @@ def run_stats(args):
         print(json.dumps(d), flush=True)
 
 
+def run_ratio_sweep(args):
+    """Mixed batches (Algorithm 3) at several insert:query ratios x: the
+    high-diameter grid + paths edges, shuffled, with 1/x random queries per
+    insert mixed in, in batches of 2^22 operations (Section 4.4's experiment)."""
+    import torch
+    import paper_2008_11839_gb300 as g
+    g.build()
+    dev = torch.device("cuda", 0)
+    n, e = graphgen.grid_paths(4096, 0.05, 64, 1 << 18, 0x6C0A0003)
+    m = len(e)
+    stream = torch.cuda.current_stream()
+    for x in [8.0, 4.0, 2.0, 1.0, 0.5, 0.25]:
+        q = int(m / x)
+        pairs = np.empty((m + q, 2), np.uint32)
+        pairs[:m] = e
+        graphgen.pairs_range(n, 0, q, 0x6C0A0007, out=pairs[m:])
+        isq = np.zeros(m + q, np.uint8)
+        isq[m:] = 1
+        perm = graphgen.permutation(m + q, 0x6C0A0008, 6).astype(np.int64)
+        d_pairs = torch.from_numpy(pairs[perm].view(np.int32)).to(dev)
+        d_isq = torch.from_numpy(isq[perm]).to(dev)
+        total = m + q
+        B = 1 << 22
+        bits = torch.empty((B + 31) // 32, dtype=torch.int32, device=dev)
+        for v_spec in args.ratio_variants.split(","):
+            v = parse_variant(g, "none/" + v_spec)
+            h = g.gconn_inc_create(n, v, stream)
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for s in range(0, total, B):
+                c = min(B, total - s)
+                g.gconn_inc_process_batch(h, c, d_pairs[s:s + c], d_isq[s:s + c], bits, stream)
+            b_.record(stream)
+            b_.synchronize()
+            g.gconn_sync(stream)
+            ms = a.elapsed_time(b_)
+            g.gconn_inc_destroy(h)
+            print(json.dumps({"ratio_insert_to_query": x, "variant": v_spec, "ops": total, "inserts": m,
+                              "ms": round(ms, 3), "ops_per_s": total / (ms * 1e-3)}), flush=True)
+        del d_pairs, d_isq
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -679,6 +722,8 @@ def main():
     ap.add_argument("--sweep-samples", default="none,kout,hb,bfs")
     ap.add_argument("--sweep-steps", type=int, default=5)
     ap.add_argument("--stats", action="store_true", help="sampling Cov / IC / Time %% per sampling method")
+    ap.add_argument("--ratio-sweep", action="store_true", help="mixed batches at several insert:query ratios")
+    ap.add_argument("--ratio-variants", default="early/naive,async/halve,remcas/naive/split_one")
     ap.add_argument("--stats-variants", default="kout/remcas/naive/split_one,hb/remcas/naive/split_one,"
                                                  "bfs/remcas/naive/split_one,none/remcas/naive/split_one")
     args = ap.parse_args()
@@ -692,6 +737,9 @@ def main():
         return
     if args.stats:
         run_stats(args)
+        return
+    if args.ratio_sweep:
+        run_ratio_sweep(args)
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)

@@ -214,6 +214,18 @@ gconn_status gconn_inc_insert_batch(gconn_inc* h, uint64_t b, const uint32_t* ed
 gconn_status gconn_inc_query(gconn_inc* h, uint64_t q, const uint32_t* pairs, uint8_t* connected,
                              void* stream);
 
+/* A mixed batch as in Algorithm 3: op i is a query when is_query[i] != 0,
+ * else an insert.  Bit i of result_bits (uint32 words, ceil(b/32) of them,
+ * bit i%32 of word i/32) is 1 iff op i is a query whose endpoints are
+ * connected.  Inserts and queries of the batch run concurrently, so an answer
+ * is linearizable: 1 whenever the endpoints were connected before the batch,
+ * 0 whenever they are not connected after it, either in between.  For
+ * Union-Rem-CAS / Rem-Lock the batch's inserts run first, then its queries
+ * (Section 3.5).  Round-based finishes: GCONN_E_UNSUPPORTED.
+ *   pairs: uint32[2b]; is_query: uint8[b]; result_bits: uint32[ceil(b/32)]. */
+gconn_status gconn_inc_process_batch(gconn_inc* h, uint64_t b, const uint32_t* pairs, const uint8_t* is_query,
+                                     uint32_t* result_bits, void* stream);
+
 /* Canonical min-id labels of the current state into uint32[n] (device or host). */
 gconn_status gconn_inc_labels(gconn_inc* h, uint32_t* labels, void* stream);
 

@@ -128,6 +128,7 @@ _SIGS = {
     "gconn_inc_insert_batch": (_i32, [_vp, _u64, _vp, _vp]),
     "gconn_inc_query": (_i32, [_vp, _u64, _vp, _vp, _vp]),
     "gconn_inc_labels": (_i32, [_vp, _vp, _vp]),
+    "gconn_inc_process_batch": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp]),
     "gconn_inc_destroy": (_i32, [_vp]),
     "gconn_cc_csr_noalloc": (_i32, [_u32, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), _vp]),
     "gconn_batch_tune_default": (_i32, [ctypes.POINTER(gconn_batch_tune)]),
@@ -327,6 +328,11 @@ def gconn_inc_insert_batch(h, b, edges, stream=None):
 
 def gconn_inc_query(h, q, pairs, connected, stream=None):
     check(lib().gconn_inc_query(h, q, ptr(pairs), ptr(connected), stream_handle(stream)), "gconn_inc_query")
+
+
+def gconn_inc_process_batch(h, b, pairs, is_query, result_bits, stream=None):
+    check(lib().gconn_inc_process_batch(h, b, ptr(pairs), ptr(is_query), ptr(result_bits), stream_handle(stream)),
+          "gconn_inc_process_batch")
 
 
 def gconn_inc_labels(h, labels, stream=None):

@@ -50,6 +50,39 @@ __global__ void __launch_bounds__(256) k_query(const uint2* __restrict__ Q, uint
     }
 }
 
+// Mixed batch (Algorithm 3): op i is an insert or a query; a warp covers 32
+// consecutive ops and writes one 32-bit word of the answer bitvector.
+// PHASE: 0 = inserts and queries together, 1 = inserts only, 2 = queries only.
+template <int L, int F, int S, int PHASE>
+__global__ void __launch_bounds__(256) k_mixed(const uint2* __restrict__ E, const uint8_t* __restrict__ isq,
+                                               uint64_t b, UFState s, uint32_t* bits) {
+    uint64_t nwords = (b + 31) / 32;
+    uint64_t nw = (uint64_t)gridDim.x * (blockDim.x / 32);
+    unsigned lane = threadIdx.x & 31u;
+    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nwords; w += nw) {
+        uint64_t i = w * 32 + lane;
+        bool ans = false;
+        if (i < b) {
+            uint2 e = __ldcs(E + i);
+            bool q = isq[i] != 0;
+            if (e.x >= s.n || e.y >= s.n) {
+                atomicOr(s.err, GC_DERR_RANGE);
+            } else if (!q && PHASE != 2) {
+                if (e.x != e.y) {
+                    Spin sp(s.cap);
+                    uf_union<L, F, S, false>(s, e.x, e.y, 0, sp);
+                }
+            } else if (q && PHASE != 1) {
+                Spin sp(s.cap);
+                if (L == LK_JTB) ans = jtb_find<F>(s, e.x, sp) == jtb_find<F>(s, e.y, sp);
+                else ans = uf_find<F, true>(s, e.x, sp) == uf_find<F, true>(s, e.y, sp);
+            }
+        }
+        unsigned word = __ballot_sync(0xFFFFFFFFu, ans);
+        if (PHASE != 1 && lane == 0) bits[w] = word;
+    }
+}
+
 template <int L, int F>
 static gconn_status launch_query(const UFState& s, const uint2* Q, uint64_t q, uint8_t* out, int block,
                                  cudaStream_t st) {
@@ -75,6 +108,47 @@ static gconn_status query_dispatch(const Variant& v, const UFState& s, const uin
         case FD_HALVE: return launch_query<LK_ASYNC, FD_HALVE>(s, Q, q, out, B, st);
         default: return launch_query<LK_ASYNC, FD_NAIVE>(s, Q, q, out, B, st);
     }
+}
+
+template <class Fn>
+static gconn_status dispatch_inc(int L, int F, int S, Fn&& fn) {
+#define GC_IN_CASE(l, f, s) \
+    if (L == l && F == f && S == s) return fn.template operator()<l, f, s>();
+    GC_IN_CASE(LK_ASYNC, FD_NAIVE, SP_NONE)
+    GC_IN_CASE(LK_ASYNC, FD_COMPRESS, SP_NONE)
+    GC_IN_CASE(LK_ASYNC, FD_SPLIT, SP_NONE)
+    GC_IN_CASE(LK_ASYNC, FD_HALVE, SP_NONE)
+    GC_IN_CASE(LK_HOOKS, FD_NAIVE, SP_NONE)
+    GC_IN_CASE(LK_HOOKS, FD_COMPRESS, SP_NONE)
+    GC_IN_CASE(LK_HOOKS, FD_SPLIT, SP_NONE)
+    GC_IN_CASE(LK_HOOKS, FD_HALVE, SP_NONE)
+    GC_IN_CASE(LK_EARLY, FD_NAIVE, SP_NONE)
+    GC_IN_CASE(LK_EARLY, FD_COMPRESS, SP_NONE)
+    GC_IN_CASE(LK_EARLY, FD_SPLIT, SP_NONE)
+    GC_IN_CASE(LK_EARLY, FD_HALVE, SP_NONE)
+    GC_IN_CASE(LK_REMCAS, FD_NAIVE, SP_SPLIT_ONE)
+    GC_IN_CASE(LK_REMCAS, FD_NAIVE, SP_HALVE_ONE)
+    GC_IN_CASE(LK_REMCAS, FD_NAIVE, SP_SPLICE)
+    GC_IN_CASE(LK_REMCAS, FD_SPLIT, SP_SPLIT_ONE)
+    GC_IN_CASE(LK_REMCAS, FD_SPLIT, SP_HALVE_ONE)
+    GC_IN_CASE(LK_REMCAS, FD_SPLIT, SP_SPLICE)
+    GC_IN_CASE(LK_REMCAS, FD_HALVE, SP_SPLIT_ONE)
+    GC_IN_CASE(LK_REMCAS, FD_HALVE, SP_HALVE_ONE)
+    GC_IN_CASE(LK_REMCAS, FD_HALVE, SP_SPLICE)
+    GC_IN_CASE(LK_REMLOCK, FD_NAIVE, SP_SPLIT_ONE)
+    GC_IN_CASE(LK_REMLOCK, FD_NAIVE, SP_HALVE_ONE)
+    GC_IN_CASE(LK_REMLOCK, FD_NAIVE, SP_SPLICE)
+    GC_IN_CASE(LK_REMLOCK, FD_SPLIT, SP_SPLIT_ONE)
+    GC_IN_CASE(LK_REMLOCK, FD_SPLIT, SP_HALVE_ONE)
+    GC_IN_CASE(LK_REMLOCK, FD_SPLIT, SP_SPLICE)
+    GC_IN_CASE(LK_REMLOCK, FD_HALVE, SP_SPLIT_ONE)
+    GC_IN_CASE(LK_REMLOCK, FD_HALVE, SP_HALVE_ONE)
+    GC_IN_CASE(LK_REMLOCK, FD_HALVE, SP_SPLICE)
+    GC_IN_CASE(LK_AFFOREST, FD_NAIVE, SP_NONE)
+    GC_IN_CASE(LK_JTB, FD_NAIVE, SP_NONE)
+    GC_IN_CASE(LK_JTB, FD_TWOTRY, SP_NONE)
+#undef GC_IN_CASE
+    return GCONN_E_UNSUPPORTED;
 }
 
 static UFState handle_state(gconn_inc* h) {
@@ -170,6 +244,50 @@ extern "C" gconn_status gconn_inc_query(gconn_inc* h, uint64_t q, const uint32_t
     }
     GC_TRY(query_dispatch(h->v, handle_state(h), (const uint2*)dp, q, dout, st));
     if (host_out) GC_CUDA(cudaMemcpyAsync(connected, dout, q, cudaMemcpyDeviceToHost, st));
+    if (host_in || host_out) return read_and_clear_err(st);
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_inc_process_batch(gconn_inc* h, uint64_t b, const uint32_t* pairs,
+                                                const uint8_t* is_query, uint32_t* result_bits, void* stream) {
+    if (!h || (b && (!pairs || !is_query || !result_bits)) || b >= (1ull << 63) || ((uintptr_t)pairs & 7u) ||
+        ((uintptr_t)result_bits & 3u))
+        return GCONN_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last = st;
+    if (b == 0) return GCONN_OK;
+    if (h->n == 0) return GCONN_E_RANGE;
+    if (is_rounds_link(h->v.link)) return GCONN_E_UNSUPPORTED;   // rounds finish a whole insert batch first
+    DevBuf pb, qb, ob;
+    const uint32_t* dp = nullptr;
+    const uint8_t* dq = nullptr;
+    bool host_in = !is_device_ptr(pairs) || !is_device_ptr(is_query), host_out = !is_device_ptr(result_bits);
+    GC_TRY(stage_in(pairs, sizeof(uint32_t) * 2 * b, st, pb, (const void**)&dp));
+    GC_TRY(stage_in(is_query, b, st, qb, (const void**)&dq));
+    uint64_t words = (b + 31) / 32;
+    uint32_t* dout = result_bits;
+    if (host_out) {
+        GC_TRY(ob.alloc(sizeof(uint32_t) * words, st));
+        dout = ob.as<uint32_t>();
+    }
+    int L, F, S;
+    uf_triple(h->v, &L, &F, &S);
+    // Rem's algorithms are correct only phase-concurrently (Section 3.5):
+    // their inserts run first, then the queries
+    bool split = L == LK_REMCAS || L == LK_REMLOCK;
+    UFState s = handle_state(h);
+    int B = h->v.block > 0 ? h->v.block : 256;
+    GC_TRY(dispatch_inc(L, F, S, [&]<int l, int f, int sp>() -> gconn_status {
+        if (split) {
+            auto k1 = k_mixed<l, f, sp, 1>;
+            GC_TRY(launch("mixed_insert", k1, grid_for(k1, B, b), B, 0, st, (const uint2*)dp, dq, b, s, dout));
+            auto k2 = k_mixed<l, f, sp, 2>;
+            return launch("mixed_query", k2, grid_for(k2, B, b), B, 0, st, (const uint2*)dp, dq, b, s, dout);
+        }
+        auto k = k_mixed<l, f, sp, 0>;
+        return launch("mixed", k, grid_for(k, B, b), B, 0, st, (const uint2*)dp, dq, b, s, dout);
+    }));
+    if (host_out) GC_CUDA(cudaMemcpyAsync(result_bits, dout, sizeof(uint32_t) * words, cudaMemcpyDeviceToHost, st));
     if (host_in || host_out) return read_and_clear_err(st);
     return GCONN_OK;
 }

@@ -106,3 +106,37 @@ def test_incremental_rejects_non_root_based():
     assert ex.value.status == g.GCONN_E_UNSUPPORTED
     with pytest.raises(g.GconnError):
         g.gconn_inc_create(10, g.make_variant(sample="kout"))
+
+
+MIXED_VARIANTS = [dict(link=l, find=f, splice=s) for (l, f, s) in UF_COMBOS]
+
+
+@pytest.mark.parametrize("kw", MIXED_VARIANTS, ids=_vid)
+def test_mixed_batches_linearizable(kw):
+    """Algorithm 3's mixed batches: every answer lies between the state before
+    and after its batch, and the final labels equal static components."""
+    n = 5000
+    inc = g.gconn_inc_create(n, g.make_variant(**kw))
+    ref = oracle.Incremental(n)
+    rng = np.random.default_rng(5)
+    allins = []
+    for bi in range(6):
+        b = int(rng.integers(1, 5000))
+        pairs = graphgen.er(n, b, 300 + bi)
+        isq = (rng.random(b) < 0.5).astype(np.uint8)
+        before = ref.query(pairs)
+        ins = pairs[isq == 0]
+        ref.insert(ins)
+        allins.append(ins)
+        after = ref.query(pairs)
+        bits = np.zeros((b + 31) // 32, np.uint32)
+        g.gconn_inc_process_batch(inc, b, pairs, isq, bits)
+        got = ((bits[np.arange(b) // 32] >> (np.arange(b) % 32).astype(np.uint32)) & 1).astype(bool)
+        q = isq == 1
+        assert not got[~q].any()                        # inserts have no bit
+        assert (got[q] >= before[q].astype(bool)).all()  # connected before => 1
+        assert (got[q] <= after[q].astype(bool)).all()   # not connected after => 0
+    lab = np.empty(n, np.uint32)
+    g.gconn_inc_labels(inc, lab)
+    assert (lab == oracle.cc_uf(n, np.concatenate(allins))).all()
+    g.gconn_inc_destroy(inc)
