@@ -74,8 +74,7 @@ __global__ void __launch_bounds__(256) k_mixed(const uint2* __restrict__ E, cons
                 }
             } else if (q && PHASE != 1) {
                 Spin sp(s.cap);
-                if (L == LK_JTB) ans = jtb_find<F>(s, e.x, sp) == jtb_find<F>(s, e.y, sp);
-                else ans = uf_find<F, true>(s, e.x, sp) == uf_find<F, true>(s, e.y, sp);
+                ans = same_set<L, F>(s, e.x, e.y, sp);
             }
         }
         unsigned word = __ballot_sync(0xFFFFFFFFu, ans);

@@ -421,6 +421,39 @@ __device__ __forceinline__ bool union_jtb(const UFState& s, uint32_t u, uint32_t
     return false;
 }
 
+// ----------------------------------------------------------- same set
+// Connectivity query that stays exact while unions run concurrently.  Two
+// roots found at different times may differ although the sets have merged in
+// between, so "different" is answered only after both are confirmed to still
+// be roots by fresh (L2) reads: a non-root never becomes a root again, so at
+// that instant the two vertices are in different sets.  Otherwise the walk
+// continues from the fresh parent.
+template <int L, int F>
+__device__ __forceinline__ bool same_set(const UFState& s, uint32_t x, uint32_t y, Spin& sp) {
+    if (L == LK_JTB) {
+        uint32_t a = jtb_find<F>(s, x, sp), b = jtb_find<F>(s, y, sp);
+        while (!sp.dead) {
+            if (a == b) return true;
+            uint32_t pa = wpar(ldw(s.W, a));
+            if (pa != a) { a = jtb_find<F>(s, pa, sp); continue; }
+            uint32_t pb = wpar(ldw(s.W, b));
+            if (pb != b) { b = jtb_find<F>(s, pb, sp); continue; }
+            return false;
+        }
+        return false;
+    }
+    uint32_t a = uf_find<F, true>(s, x, sp), b = uf_find<F, true>(s, y, sp);
+    while (!sp.dead) {
+        if (a == b) return true;
+        uint32_t pa = ldp(s.P, a);
+        if (pa != a) { a = uf_find<F, true>(s, pa, sp); if (!sp.step(s)) break; continue; }
+        uint32_t pb = ldp(s.P, b);
+        if (pb != b) { b = uf_find<F, true>(s, pb, sp); if (!sp.step(s)) break; continue; }
+        return false;
+    }
+    return false;
+}
+
 // ----------------------------------------------------------- dispatcher
 template <int L, int F, int S, bool SF>
 __device__ __forceinline__ bool uf_union(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
