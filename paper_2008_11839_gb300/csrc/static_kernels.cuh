@@ -121,23 +121,40 @@ static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __re
     unsigned lt = (1u << lane) - 1;
     uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
     uint64_t nwords = ((uint64_t)s.n + 31) / 32;
-    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nwords; w += nwarps) {
-        uint64_t v = w * 32 + lane;
-        uint32_t c0 = GC_DINF, c1 = GC_DINF;
-        uint64_t lo = 0;
-        if (v < s.n) {
-            lo = off[v];
-            uint64_t hi = off[v + 1];
-            if (hi > lo) c0 = cols[lo];
-            if (k > 1 && hi > lo + 1) c1 = cols[lo + 1];
+    // Two-deep software pipeline over this warp's words: while word i's
+    // unions drain, the column loads of word i+1 and the offset loads of
+    // word i+2 are in flight.
+    uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    auto load_off = [&](uint64_t ww, uint64_t& lo, uint64_t& hi) {
+        uint64_t x = ww * 32 + lane;
+        lo = hi = 0;
+        if (ww < nwords && x < s.n) {
+            lo = off[x];
+            hi = off[x + 1];
         }
+    };
+    auto load_cols = [&](uint64_t lo, uint64_t hi, uint32_t& c0, uint32_t& c1) {
+        c0 = hi > lo ? cols[lo] : GC_DINF;
+        c1 = (k > 1 && hi > lo + 1) ? cols[lo + 1] : GC_DINF;
+    };
+    uint64_t lo0, hi0, lo1, hi1;
+    uint32_t c0, c1;
+    load_off(w, lo0, hi0);
+    load_off(w + nwarps, lo1, hi1);
+    load_cols(lo0, hi0, c0, c1);
+    for (; w < nwords; w += nwarps) {
+        uint32_t n0, n1;
+        uint64_t lo2, hi2;
+        load_cols(lo1, hi1, n0, n1);             // word i+1
+        load_off(w + 2 * nwarps, lo2, hi2);      // word i+2
+        uint64_t v = w * 32 + lane;
         if ((c0 != GC_DINF && c0 >= s.n) || (c1 != GC_DINF && c1 >= s.n)) atomicOr(s.err, GC_DERR_RANGE);
         bool j0 = c0 < s.n && c0 != (uint32_t)v;
         bool j1 = c1 < s.n && c1 != (uint32_t)v;
         unsigned m0 = __ballot_sync(0xFFFFFFFFu, j0), m1 = __ballot_sync(0xFFFFFFFFu, j1);
-        unsigned n0 = __popc(m0), total = n0 + __popc(m1);
-        if (j0) my[__popc(m0 & lt)] = KoutJob{(uint32_t)v, c0, (uint32_t)lo};
-        if (j1) my[n0 + __popc(m1 & lt)] = KoutJob{(uint32_t)v, c1, (uint32_t)(lo + 1)};
+        unsigned nj0 = __popc(m0), total = nj0 + __popc(m1);
+        if (j0) my[__popc(m0 & lt)] = KoutJob{(uint32_t)v, c0, (uint32_t)lo0};
+        if (j1) my[nj0 + __popc(m1 & lt)] = KoutJob{(uint32_t)v, c1, (uint32_t)(lo0 + 1)};
         __syncwarp();
         for (unsigned j = lane; j < total; j += 32) {
             KoutJob jb = my[j];
@@ -155,6 +172,8 @@ static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __re
             uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
         }
         __syncwarp();
+        lo0 = lo1; hi0 = hi1; c0 = n0; c1 = n1;
+        lo1 = lo2; hi1 = hi2;
     }
 }
 
@@ -500,19 +519,21 @@ static __global__ void __launch_bounds__(256) k_finish_over(const uint64_t* __re
 
 // LabelFinalization (Algorithm 1): labels[v] = root(v).  With min-linking the
 // root is the smallest id of its tree, i.e. already canonical.
-// Four independent walks per thread advance in lock step, so four parent
-// loads are in flight at a time.
+// When labels is the parent array, each thread takes four consecutive vertices
+// with one 16-byte load; the four walks advance in lock step (four parent loads in
+// flight), and the four labels are written back only when one changed (after
+// the vertex-gathering pass most vertices already point at their root).
 static __global__ void k_finalize(UFState s, uint32_t* labels) {
     constexpr int W = 4;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; base < s.n; base += W * stride) {
-        uint32_t cur[W], nxt[W];
+    uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool vec = labels == s.P && ((uintptr_t)labels & 15u) == 0;
+    uint64_t nv = vec ? s.n / 4 : 0;
+    for (uint64_t q = t0; q < nv; q += stride) {
+        uint4 p4 = __ldcg(reinterpret_cast<const uint4*>(s.P) + q);
+        uint32_t cur[W] = {p4.x, p4.y, p4.z, p4.w}, nxt[W];
 #pragma unroll
-        for (int j = 0; j < W; ++j) {
-            uint64_t x = base + (uint64_t)j * stride;
-            cur[j] = x < s.n ? (uint32_t)x : GC_DINF;
-            nxt[j] = x < s.n ? ldq<true>(s.P, (uint32_t)x) : GC_DINF;
-        }
+        for (int j = 0; j < W; ++j) nxt[j] = ldq<true>(s.P, cur[j]);
         for (uint32_t step = 0; step <= s.n; ++step) {
             bool any = false;
 #pragma unroll
@@ -524,16 +545,13 @@ static __global__ void k_finalize(UFState s, uint32_t* labels) {
             }
             if (!any) break;
 #pragma unroll
-            for (int j = 0; j < W; ++j)
-                if (cur[j] != GC_DINF) nxt[j] = ldq<true>(s.P, cur[j]);
+            for (int j = 0; j < W; ++j) nxt[j] = ldq<true>(s.P, cur[j]);
             if (step == s.n) atomicOr(s.err, GC_DERR_NONCONV);
         }
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            uint64_t x = base + (uint64_t)j * stride;
-            if (x < s.n) labels[x] = cur[j];
-        }
+        if (cur[0] != p4.x || cur[1] != p4.y || cur[2] != p4.z || cur[3] != p4.w)
+            reinterpret_cast<uint4*>(labels)[q] = make_uint4(cur[0], cur[1], cur[2], cur[3]);
     }
+    for (uint64_t v = nv * 4 + t0; v < s.n; v += stride) labels[v] = uf_root<LK_ASYNC, true>(s, (uint32_t)v);
 }
 
 // Union-JTB roots are not minimal: canonicalise through the root.
