@@ -373,6 +373,15 @@ const char* gconn_status_str(gconn_status s);
 /* Kernel launches made by this library in this process (all devices). */
 uint64_t gconn_launch_count(void);
 
+/* Memory utility; the paper has no counterpart.  Scratch and host-input
+ * staging buffers are taken from one stream-ordered memory pool per device
+ * that keeps freed memory reserved for later calls (so repeated calls do not
+ * map and unmap device memory).  gconn_release_cached returns the pool's idle
+ * memory on the current device to the system.  Memory whose stream-ordered
+ * free has not executed yet stays reserved: synchronise the streams used
+ * first.  Returns GCONN_OK or GCONN_E_CUDA. */
+gconn_status gconn_release_cached(void);
+
 /* Per-kernel timing with CUDA events recorded on each launch's own stream.
  * gconn_profile_enable(1) starts recording (0 stops), gconn_profile_reset
  * clears the totals, gconn_profile_get(i, ...) synchronises pending events and

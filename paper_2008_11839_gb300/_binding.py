@@ -157,6 +157,7 @@ _SIGS = {
     "gconn_sync": (_i32, [_vp]),
     "gconn_status_str": (ctypes.c_char_p, [_i32]),
     "gconn_launch_count": (_u64, []),
+    "gconn_release_cached": (_i32, []),
     "gconn_profile_enable": (_i32, [_i32]),
     "gconn_profile_reset": (_i32, []),
     "gconn_profile_get": (_i32, [_i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_u64),
@@ -435,6 +436,10 @@ def gconn_status_str(status: int) -> str:
 
 def gconn_launch_count() -> int:
     return int(lib().gconn_launch_count())
+
+
+def gconn_release_cached():
+    check(lib().gconn_release_cached(), "gconn_release_cached")
 
 
 def gconn_profile_enable(on: bool = True):

@@ -36,6 +36,7 @@ constexpr uint64_t DEFAULT_SEED = 0x6C0A0001ull;
 
 gconn_status cuda_status(cudaError_t e);          // maps OOM -> E_NOMEM, else E_CUDA
 uint32_t* err_word();                             // device error word of the current device
+cudaMemPool_t scratch_pool();                     // caching scratch pool of the current device
 gconn_status read_and_clear_err(cudaStream_t st); // sync st, then read/clear the word
 
 // ----------------------------------------------------------------- devices

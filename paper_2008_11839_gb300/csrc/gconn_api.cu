@@ -37,17 +37,52 @@ static constexpr int MAX_DEV = 64;
 static uint32_t* g_err_ptr[MAX_DEV];
 static int g_sms[MAX_DEV];
 
-uint32_t* err_word() {
+static cudaMemPool_t g_pool[MAX_DEV];
+
+// Scratch and staging buffers come from one stream-ordered pool per device
+// whose release threshold is unlimited: memory a call frees stays reserved in
+// the pool for the next call instead of being unmapped at the next
+// synchronisation, so repeated calls (and host-input calls that stage whole
+// CSR arrays) do not map and unmap device memory every time.
+// gconn_release_cached returns the idle part to the device.
+cudaMemPool_t scratch_pool() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= MAX_DEV) return nullptr;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_err_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_gconn_err) != cudaSuccess) return nullptr;
-        g_err_ptr[dev] = (uint32_t*)p;
+    if (!g_pool[dev]) {
+        cudaMemPoolProps pr{};
+        pr.allocType = cudaMemAllocationTypePinned;
+        pr.location.type = cudaMemLocationTypeDevice;
+        pr.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &pr) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
     }
-    return g_err_ptr[dev];
+    return g_pool[dev];
+}
+
+uint32_t* err_word() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= MAX_DEV) return nullptr;
+    uint32_t* w = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_err_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_gconn_err) != cudaSuccess) return nullptr;
+            g_err_ptr[dev] = (uint32_t*)p;
+        }
+        w = g_err_ptr[dev];
+    }
+    scratch_pool();   // created here too, so that it exists before any stream capture
+    return w;
 }
 
 int num_sms() {
@@ -93,7 +128,8 @@ gconn_status DevBuf::alloc(size_t bytes, cudaStream_t stream) {
     release();
     st = stream;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    cudaMemPool_t pool = scratch_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, stream) : cudaMallocAsync(&p, bytes, stream);
     if (e != cudaSuccess) {
         p = nullptr;
         return cuda_status(e);
@@ -380,6 +416,14 @@ extern "C" const char* gconn_status_str(gconn_status s) {
 }
 
 extern "C" uint64_t gconn_launch_count(void) { return g_launches.load(); }
+
+extern "C" gconn_status gconn_release_cached(void) {
+    if (!err_word()) return GCONN_E_CUDA;
+    cudaMemPool_t pool = scratch_pool();
+    if (!pool) return GCONN_E_CUDA;
+    GC_CUDA(cudaMemPoolTrimTo(pool, 0));
+    return GCONN_OK;
+}
 
 extern "C" gconn_status gconn_profile_enable(int on) {
     g_profiling.store(on != 0);

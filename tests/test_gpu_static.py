@@ -159,6 +159,19 @@ def test_host_pointers_match():
     assert oracle.sf_check(n, e, forest[: int(cnt[0])], REF[name]) == 0
 
 
+def test_release_cached_then_rerun():
+    """Scratch memory is cached between calls; releasing it leaves later calls exact."""
+    import torch
+    name, n, e = GRAPHS[0]
+    off, cols = CSR[name]
+    for _ in range(2):
+        lab = np.empty(n, np.uint32)
+        g.gconn_cc_csr(n, off, cols, lab, g.make_variant(sample="kout"))
+        assert (lab == REF[name]).all()
+        torch.cuda.synchronize()
+        g.gconn_release_cached()
+
+
 def test_repeated_runs_stay_valid():
     """Concurrent forests differ between runs; every one must be valid."""
     name, n, e = GRAPHS[2]
