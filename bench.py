@@ -222,11 +222,38 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     v = parse_variant(g, args.variant)
     stream = torch.cuda.current_stream()
-    # one static pass captured once into a CUDA graph (with per-kernel event
-    # pairs, so kernel durations are measured on the launching stream)
-    g.gconn_profile_enable(True)
-    plan = g.gconn_plan_create_cc_csr(n, d_off, d_cols, labels, v)
-    g.gconn_profile_enable(False)
+    # One static pass is captured once into a CUDA graph.  Every timed kernel
+    # adds two event-record nodes, and each serialises the replay for a few
+    # microseconds, so the passes are timed twice: (1) every kernel bracketed,
+    # for the per-kernel shares (a separate replay loop); (2) the timed region
+    # proper, with events around the dominant kernel only (its live duration
+    # gives the roofline) and the step timed by events around each replay.
+    def make_plan(select):
+        g.gconn_profile_select(select)
+        g.gconn_profile_enable(True)
+        p = g.gconn_plan_create_cc_csr(n, d_off, d_cols, labels, v)
+        g.gconn_profile_enable(False)
+        g.gconn_profile_select(None)
+        return p
+
+    plan_all = make_plan(None)
+    for i in range(args.warmup):
+        flush.fill_(i)
+        g.gconn_plan_run(plan_all, stream)
+        g.gconn_sync(stream)
+        g.gconn_profile_sync()
+    g.gconn_profile_reset()
+    for i in range(args.steps):
+        flush.fill_(i + 500)
+        g.gconn_plan_run(plan_all, stream)
+        g.gconn_sync(stream)
+        g.gconn_profile_sync()
+    prof_all = profile_table(g)       # per-kernel totals, every kernel bracketed
+    g.gconn_profile_reset()
+    g.gconn_plan_destroy(plan_all)
+    dom_name = max(prof_all.items(), key=lambda kv: kv[1]["ms"])[0] if prof_all else None
+
+    plan = make_plan(dom_name)
 
     def step():
         g.gconn_plan_run(plan, stream)
@@ -235,6 +262,7 @@ def run_ours(args, rank, world, local_rank):
         flush.fill_(i)
         step()
     g.gconn_sync(stream)
+    g.gconn_profile_sync()
 
     # parity of the benchmarked configuration against the oracle's labels is
     # covered by the tests; here a cheap invariant check guards the numbers
@@ -281,8 +309,8 @@ def run_ours(args, rank, world, local_rank):
     ms = max_over_ranks(float(np.mean(step_ms)), dist, dev)
     g.gconn_plan_destroy(plan)
 
-    # dominant kernel's roofline from the live per-kernel events
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
+    # dominant kernel's roofline from its live events in the timed region
+    dom = (dom_name, prof[dom_name]) if dom_name in prof else (None, None)
     roof = None
     if dom[0]:
         per_launch_ms = dom[1]["ms"] / max(dom[1]["launches"], 1)
@@ -292,7 +320,9 @@ def run_ours(args, rank, world, local_rank):
             roof = {"kernel": dom[0], "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(ach / hbm, 4), "traffic": None, "peak_source": peak_src,
                     "alg_bytes_per_launch": b, "avg_launch_ms": round(per_launch_ms, 5)}
-    step_share = {k: round(vv["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-9), 4) for k, vv in prof.items()}
+    step_share = {k: round(vv["ms"] / max(sum(x["ms"] for x in prof_all.values()), 1e-9), 4)
+                  for k, vv in prof_all.items()}
+    kernel_us = {k: round(1e3 * vv["ms"] / max(vv["launches"], 1), 2) for k, vv in prof_all.items()}
 
     result = {"metric": "static CC edges/s (RMAT scale 22, 2^26 undirected edges)",
               "value": M * world / (ms * 1e-3), "unit": "edges/s", "n_gpus": world, "steps": args.steps,
@@ -305,7 +335,10 @@ def run_ours(args, rank, world, local_rank):
                          "variant": args.variant, "input": "CSR (u64 offsets, u32 cols), resident",
                          "launch": "one captured CUDA graph per step (gconn_plan_run)",
                          "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
-              "roofline": roof, "kernel_share": step_share, "clocks": clk,
+              "roofline": roof, "kernel_share": step_share, "kernel_us": kernel_us,
+              "instrumentation": {"timed_region": f"events around {dom_name} only",
+                                  "kernel_share": "separate replay loop, every kernel bracketed by events"},
+              "clocks": clk,
               "wall_s_timed": round(wall, 4)}
 
     # end to end through the C ABI with pinned host buffers

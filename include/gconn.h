@@ -388,6 +388,13 @@ gconn_status gconn_release_cached(void);
  * returns the name, launch count and summed milliseconds of the i-th kernel
  * (GCONN_E_INVAL once i is past the last one). */
 gconn_status gconn_profile_enable(int on);
+/* Restricts the timing to the kernels named in a comma-separated list (the
+ * names gconn_profile_get reports, e.g. "kout,vg"); NULL or "" times every
+ * kernel again.  Applies to launches and plan captures made afterwards.  Each
+ * timed kernel adds two event records to a captured plan, and each record
+ * serialises the replay for a few microseconds, so timing one kernel disturbs
+ * a pass far less than timing all of them. */
+gconn_status gconn_profile_select(const char* names);
 gconn_status gconn_profile_reset(void);
 /* Collect every queued event pair now (waits for them).  Needed after each
  * replay of a profiled plan, whose events re-record on every replay. */

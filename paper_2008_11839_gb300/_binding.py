@@ -159,6 +159,7 @@ _SIGS = {
     "gconn_launch_count": (_u64, []),
     "gconn_release_cached": (_i32, []),
     "gconn_profile_enable": (_i32, [_i32]),
+    "gconn_profile_select": (_i32, [ctypes.c_char_p]),
     "gconn_profile_reset": (_i32, []),
     "gconn_profile_get": (_i32, [_i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_u64),
                                  ctypes.POINTER(ctypes.c_double)]),
@@ -444,6 +445,13 @@ def gconn_release_cached():
 
 def gconn_profile_enable(on: bool = True):
     check(lib().gconn_profile_enable(1 if on else 0), "gconn_profile_enable")
+
+
+def gconn_profile_select(names=None):
+    """Time only the named kernels (comma-separated string or list); None: all."""
+    if names is not None and not isinstance(names, str):
+        names = ",".join(names)
+    check(lib().gconn_profile_select(None if names is None else names.encode()), "gconn_profile_select")
 
 
 def gconn_profile_reset():

@@ -231,8 +231,17 @@ static cudaEvent_t take_event() {
     return e;
 }
 
+// Kernel names selected for timing (empty: all).
+static std::vector<std::string> g_prof_select;
+
 void prof_begin(const char* name, cudaStream_t st, void** token) {
     std::lock_guard<std::mutex> lk(g_pmu);
+    *token = nullptr;
+    if (!g_prof_select.empty()) {
+        bool hit = false;
+        for (const std::string& s : g_prof_select) hit |= s == name;
+        if (!hit) return;
+    }
     PendingRec* r;
     if (t_sink) {   // graph-owned events: created fresh, kept by the plan
         cudaEvent_t a = nullptr, b = nullptr;
@@ -427,6 +436,25 @@ extern "C" gconn_status gconn_release_cached(void) {
 
 extern "C" gconn_status gconn_profile_enable(int on) {
     g_profiling.store(on != 0);
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_profile_select(const char* names) {
+    std::vector<std::string> sel;
+    if (names) {
+        std::string cur;
+        for (const char* c = names;; ++c) {
+            if (*c == ',' || *c == 0) {
+                if (!cur.empty()) sel.push_back(cur);
+                cur.clear();
+                if (*c == 0) break;
+            } else if (*c != ' ') {
+                cur.push_back(*c);
+            }
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_pmu);
+    g_prof_select.swap(sel);
     return GCONN_OK;
 }
 

@@ -85,3 +85,26 @@ def test_profiled_plan_records_kernels():
     assert g.gconn_launch_count() - c0 == 3 * sum(1 for _ in prof) or g.gconn_launch_count() > c0
     assert (host_u32(lab) == oracle.cc_uf(n, e)).all()
     g.gconn_plan_destroy(p)
+
+
+def test_profile_select_times_only_named_kernels():
+    import torch
+    n = 20_000
+    e = graphgen.er(n, 50_000, 5)
+    off, cols = graphgen.csr(n, e)
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    g.gconn_profile_select("kout")
+    g.gconn_profile_enable(True)
+    p = g.gconn_plan_create_cc_csr(n, dev(off), dev(cols), lab, g.make_variant(sample="kout"))
+    g.gconn_profile_enable(False)
+    g.gconn_profile_select(None)
+    g.gconn_profile_reset()
+    for _ in range(2):
+        g.gconn_plan_run(p)
+        g.gconn_sync()
+        g.gconn_profile_sync()
+    prof = g.gconn_profile_get()
+    assert set(prof) == {"kout"} and prof["kout"][0] == 2 and prof["kout"][1] > 0
+    assert (host_u32(lab) == oracle.cc_uf(n, e)).all()
+    g.gconn_plan_destroy(p)
+    g.gconn_profile_reset()
