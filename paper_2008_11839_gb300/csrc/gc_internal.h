@@ -107,6 +107,33 @@ gconn_status launch(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 
     return e == cudaSuccess ? GCONN_OK : cuda_status(e);
 }
 
+// As launch(), with programmatic stream serialisation: the kernel may be
+// scheduled while the previous kernel in the stream is still running (also as
+// a programmatic edge inside a captured graph).  Only for kernels that begin
+// with pdl_entry(), whose griddepcontrol.wait restores the ordering.
+template <class... KArgs, class... Args>
+gconn_status launch_pdl(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                        cudaStream_t st, Args&&... args) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    count_capture_launch();
+    cudaGetLastError();
+    void* tok = nullptr;
+    if (g_profiling.load(std::memory_order_relaxed)) prof_begin(name, st, &tok);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    if (tok) prof_end(tok, st);
+    return e == cudaSuccess ? GCONN_OK : cuda_status(e);
+}
+
 // --------------------------------------------------------------- variant
 struct Variant {
     int sample, k, hb_n, link, find, splice, lt_rules, block;

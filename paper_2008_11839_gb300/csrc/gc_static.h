@@ -12,7 +12,7 @@ inline bool is_rounds_link(int link) {
     return link == GCONN_LINK_SV || link == GCONN_LINK_LT || link == GCONN_LINK_LP || link == GCONN_LINK_STERGIOU;
 }
 UFState make_state(uint32_t n, uint32_t* P, uint32_t* H, u64w* W, uint32_t* sf, const Variant& v);
-gconn_status init_state(const UFState& s, cudaStream_t st);
+gconn_status init_state(const UFState& s, cudaStream_t st, uint32_t* zero = nullptr, uint32_t nzero = 0);
 gconn_status union_coo(const Variant& v, const UFState& s, const uint32_t* edges, uint64_t m, uint32_t eid_base,
                        cudaStream_t st);
 gconn_status compress_all(const Variant& v, const UFState& s, cudaStream_t st);

@@ -153,7 +153,7 @@ extern "C" gconn_status gconn_cc_csr_noalloc(uint32_t n, const uint64_t* offsets
 
     // the counters must start at zero; everything else is written before read
     GC_CUDA(cudaMemsetAsync(hdr, 0, 4 * sizeof(uint32_t), st));
-    GC_TRY(launch("init", k_init, grid_for(k_init, 256, n), 256, 0, st, n, s.P, s.H, s.W, s.sf));
+    GC_TRY(launch("init", k_init, grid_for(k_init, 256, n), 256, 0, st, n, s.P, s.H, s.W, s.sf, nullptr, 0u));
     return dispatch_noalloc(L, F, S, [&]<int l, int fr, int sp>() -> gconn_status {
         if (v.sample == GCONN_SAMPLE_KOUT) {
             auto k = k_kout<l, fr, sp, false>;

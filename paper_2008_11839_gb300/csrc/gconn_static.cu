@@ -86,9 +86,9 @@ UFState make_state(uint32_t n, uint32_t* P, uint32_t* H, u64w* W, uint32_t* sf, 
     return s;
 }
 
-gconn_status init_state(const UFState& s, cudaStream_t st) {
+gconn_status init_state(const UFState& s, cudaStream_t st, uint32_t* zero, uint32_t nzero) {
     if (s.n == 0) return GCONN_OK;
-    return launch("init", k_init, grid_for(k_init, 256, s.n), 256, 0, st, s.n, s.P, s.H, s.W, s.sf);
+    return launch_pdl("init", k_init, grid_for(k_init, 256, s.n), 256, 0, st, s.n, s.P, s.H, s.W, s.sf, zero, nzero);
 }
 
 gconn_status union_coo(const Variant& v, const UFState& s, const uint32_t* edges, uint64_t m,
@@ -115,7 +115,7 @@ gconn_status finalize_labels(const Variant& v, const UFState& s, uint32_t* label
     unsigned g = grid_for(k_finalize, 256, s.n);
     if (v.link != GCONN_LINK_JTB) {
         // labels may alias P: the walk then compresses in place
-        return launch("finalize", k_finalize, g, 256, 0, st, s, labels);
+        return launch_pdl("finalize", k_finalize, g, 256, 0, st, s, labels);
     }
     GC_TRY(compress_all(v, s, st));
     GC_TRY(launch("jtb_fill", k_fill, g, 256, 0, st, s.n, labels, INF));
@@ -149,7 +149,7 @@ struct CsrScratch {
 };
 
 gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,
-                        uint32_t* lmax_dev, cudaStream_t st) {
+                        uint32_t* lmax_dev, unsigned long long* dq_count, cudaStream_t st) {
     uint32_t n = s.n;
     int L, F, S;
     uf_triple(v, &L, &F, &S);
@@ -158,17 +158,15 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off,
     bool jtb = v.link == GCONN_LINK_JTB;
     if (v.sample == GCONN_SAMPLE_KOUT) {
         // deferred long unions: capacity n/8 jobs, overflow runs in place
-        DevBuf qbuf, qcnt;
+        DevBuf qbuf;
         uint32_t qcap = n / 8 + 64;
         GC_TRY(qbuf.alloc(sizeof(KoutJob) * (size_t)qcap, st));
-        GC_TRY(qcnt.alloc(sizeof(unsigned long long), st));
-        GC_CUDA(cudaMemsetAsync(qcnt.p, 0, sizeof(unsigned long long), st));
-        JobQueue dq{qbuf.as<KoutJob>(), qcnt.as<unsigned long long>(), qcap};
+        JobQueue dq{qbuf.as<KoutJob>(), dq_count, qcap};   // count zeroed by the init kernel
         GC_TRY(dispatch_uf(L, F, S, sf, [&]<int l, int f, int sp, bool w>() {
             auto k = k_kout<l, f, sp, w>;
-            GC_TRY(launch("kout", k, grid_for(k, KOUT_BLOCK, n), KOUT_BLOCK, 0, st, off, cols, v.k, s, dq));
+            GC_TRY(launch_pdl("kout", k, grid_for(k, KOUT_BLOCK, n), KOUT_BLOCK, 0, st, off, cols, v.k, s, dq));
             auto kj = k_union_jobs<l, f, sp, w>;
-            return launch("kout_deferred", kj, grid_for(kj, 256, qcap), 256, 0, st, s, dq);
+            return launch_pdl("kout_deferred", kj, grid_for(kj, 256, qcap), 256, 0, st, s, dq);
         }));
     } else if (v.sample == GCONN_SAMPLE_HB) {
         GC_TRY(launch("hb1", k_hb1, grid_for(k_hb1, 256, n), 256, 0, st, off, cols, n, s.P, s.sf, s.err));
@@ -187,8 +185,8 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off,
     }
     // the full compression after sampling is fused into vertex gathering
     if (jtb)
-        return launch("lmax", k_lmax<LK_JTB>, 1, LMAX_SAMPLES, 0, st, s, v.seed, lmax_dev);
-    return launch("lmax", k_lmax<LK_ASYNC>, 1, LMAX_SAMPLES, 0, st, s, v.seed, lmax_dev);
+        return launch_pdl("lmax", k_lmax<LK_JTB>, 1, LMAX_SAMPLES, 0, st, s, v.seed, lmax_dev);
+    return launch_pdl("lmax", k_lmax<LK_ASYNC>, 1, LMAX_SAMPLES, 0, st, s, v.seed, lmax_dev);
 }
 
 // Runs the sampling phase (unless NONE), L_max, vertex gathering and the
@@ -238,21 +236,21 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
     if (n == 0) return GCONN_OK;
     CsrScratch sc;
     bool sampled = v.sample != GCONN_SAMPLE_NONE;
-    uint32_t* lmax = nullptr;
+    // the pass's counters in one 64-byte header, cleared by the init kernel:
+    // [0] L_max, [1..3] gathering counters, [8..9] deferred-union count (u64)
+    GC_TRY(sc.counters.alloc(16 * sizeof(uint32_t), st));
+    uint32_t* hdr = sc.counters.as<uint32_t>();
+    uint32_t* lmax = sampled ? hdr : nullptr;
+    uint32_t* cnt = hdr + 1;
+    unsigned long long* dq_count = reinterpret_cast<unsigned long long*>(hdr + 8);
+    GC_TRY(init_state(s, st, hdr, 16));
     // the rounds-based finishes (SV, LT) sample with Union-Async
     Variant sv = v;
     bool rounds = is_rounds_link(v.link);
     if (rounds) { sv.link = GCONN_LINK_ASYNC; sv.find = GCONN_FIND_NAIVE; sv.splice = 0; }
-    if (sampled) {
-        GC_TRY(sc.lmax.alloc(sizeof(uint32_t), st));
-        lmax = sc.lmax.as<uint32_t>();
-        GC_TRY(csr_sample(sv, s, off, cols, lmax, st));
-    }
+    if (sampled) GC_TRY(csr_sample(sv, s, off, cols, lmax, dq_count, st));
     // vertex gathering
     uint64_t task_cap = (uint64_t)n + 1024;
-    GC_TRY(sc.counters.alloc(4 * sizeof(uint32_t), st));
-    uint32_t* cnt = sc.counters.as<uint32_t>();
-    GC_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(uint32_t), st));
     uint32_t* active = nullptr;
     if (sampled) {
         GC_TRY(sc.active.alloc(sizeof(uint32_t) * (((size_t)n + 31) / 32), st));
@@ -267,7 +265,7 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
     bool jtb = sv.link == GCONN_LINK_JTB;
     {
         auto k = jtb ? k_vg<LK_JTB, true> : k_vg<LK_ASYNC, true>;
-        GC_TRY(launch("vg", k, grid_for(k, 256, (uint64_t)n), 256, 0, st, off, s, lmax, active, small, cnt + 0,
+        GC_TRY(launch_pdl("vg", k, grid_for(k, 256, (uint64_t)n), 256, 0, st, off, s, lmax, active, small, cnt + 0,
                       tasks, (uint32_t)task_cap, cnt + 1, over, cnt + 2));
     }
     if (stats) {
@@ -285,7 +283,7 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
     int B = block_of(v);
     return dispatch_uf(L, F, S, s.sf != nullptr, [&]<int l, int f, int sp, bool w>() {
         auto k = k_finish<l, f, sp, w>;
-        return launch("finish", k, grid_for(k, B, (uint64_t)n * 32), B, 0, st, off, cols, s,
+        return launch_pdl("finish", k, grid_for(k, B, (uint64_t)n * 32), B, 0, st, off, cols, s,
                       (const uint32_t*)active, (const uint32_t*)small, (const uint32_t*)(cnt + 0),
                       (const unsigned long long*)tasks, (const uint32_t*)(cnt + 1), (uint32_t)task_cap,
                       (const uint32_t*)over, (const uint32_t*)(cnt + 2));
@@ -391,7 +389,7 @@ static gconn_status static_run(uint32_t n, uint64_t m, const uint32_t* edges, co
     }
     L2Window l2win;
     l2win.apply(st, P, sizeof(uint32_t) * (size_t)n);
-    GC_TRY(init_state(s, st));
+    if (!csr) GC_TRY(init_state(s, st));   // csr_connect initialises P and its counters
     if (csr && want_forest)
         GC_TRY(launch("check_arcs", k_check_arcs, 1, 1, 0, st, d_off, n, s.err));
 
@@ -459,8 +457,7 @@ extern "C" gconn_status gconn_cc_csr_stats(uint32_t n, const uint64_t* offsets, 
     cudaEventCreate(&e2);
     CsrStats cs{cb.as<unsigned long long>(), e1, e1b, (uint32_t*)(cb.as<unsigned long long>() + 8)};
     GC_CUDA(cudaEventRecord(e0, st));
-    gconn_status r = init_state(s, st);
-    if (r == GCONN_OK) r = csr_connect(v, s, offsets, cols, st, &cs);
+    gconn_status r = csr_connect(v, s, offsets, cols, st, &cs);
     if (r == GCONN_OK) r = finalize_labels(v, s, labels, st);
     if (r == GCONN_OK) r = cuda_status(cudaEventRecord(e2, st));
     unsigned long long h[8] = {0};

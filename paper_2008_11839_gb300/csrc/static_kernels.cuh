@@ -23,15 +23,32 @@ __device__ __forceinline__ uint32_t hash_u32(uint64_t seed, uint64_t i) {
     return (uint32_t)((z ^ (z >> 31)) >> 32);
 }
 
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialisation attribute may be scheduled while the grid before it in
+// the stream is still running; griddepcontrol.wait blocks until that grid has
+// completed and its writes are visible, and launch_dependents then lets the
+// next kernel's blocks be scheduled early in turn.  Both are no-ops for a
+// kernel launched normally, so every kernel that starts with pdl_entry() may
+// be launched either way.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ bool err_abort(const uint32_t* err) {
     return (__ldcg(err) & GC_DERR_NONCONV) != 0;
 }
 
 // InitLabel (Algorithm 1) and InitEdge (Algorithm 2): P[v] = v, hooks and
 // forest slots to "none", JTB words to (rank 0, parent v).
-static __global__ void k_init(uint32_t n, uint32_t* P, uint32_t* H, u64w* W, uint32_t* sf) {
+// `zero` (nzero words, may be null) is cleared too: the pass's counters.
+static __global__ void k_init(uint32_t n, uint32_t* P, uint32_t* H, u64w* W, uint32_t* sf, uint32_t* zero,
+                              uint32_t nzero) {
+    pdl_entry();
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (zero && blockIdx.x == 0)
+        for (uint32_t i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0;
     if (P && !H && !W && !sf && ((uintptr_t)P & 15u) == 0) {   // P only: 16-byte stores
         uint64_t nv = n / 4;
         uint4* P4 = reinterpret_cast<uint4*>(P);
@@ -100,6 +117,7 @@ template <int L, int F, int S, bool SF>
 static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __restrict__ off,
                                                             const uint32_t* __restrict__ cols, int k, UFState s,
                                                             JobQueue dq) {
+    pdl_entry();
     __shared__ KoutJob jobs[KOUT_BLOCK / 32][32 * KOUT_WARP_K];
     if (k > KOUT_WARP_K) {
         uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -185,6 +203,7 @@ static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __re
 // Unions deferred by k_kout, re-run from their endpoints with the full cap.
 template <int L, int F, int S, bool SF>
 static __global__ void __launch_bounds__(256) k_union_jobs(UFState s, JobQueue dq) {
+    pdl_entry();
     unsigned long long cnt = *dq.count;
     if (cnt > dq.cap) cnt = dq.cap;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -268,6 +287,7 @@ static __global__ void k_w_from_p(uint32_t n, const uint32_t* P, u64w* W) {
 // open-addressing table; the best (count, smallest label) wins.
 template <int L>
 static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_t seed, uint32_t* lmax_out) {
+    pdl_entry();
     constexpr uint32_t SLOTS = 2 * LMAX_SAMPLES;
     __shared__ uint32_t key[SLOTS];
     __shared__ uint32_t cnt[SLOTS];
@@ -317,6 +337,7 @@ static __global__ void __launch_bounds__(256) k_vg(const uint64_t* __restrict__ 
                                             uint32_t* active, uint32_t* small, uint32_t* nsmall,
                                             unsigned long long* tasks, uint32_t task_cap, uint32_t* ntasks,
                                             uint32_t* over, uint32_t* nover) {
+    pdl_entry();
     uint32_t lmax = lmax_p ? *lmax_p : GC_DINF;
     uint64_t nwords = ((uint64_t)s.n + 31) / 32;
     uint64_t wstride = (uint64_t)gridDim.x * (blockDim.x / 32);
@@ -428,6 +449,7 @@ __global__ void __launch_bounds__(256) k_finish(const uint64_t* __restrict__ off
                                                const uint32_t* nsmall, const unsigned long long* tasks,
                                                const uint32_t* ntasks, uint32_t task_cap, const uint32_t* over,
                                                const uint32_t* nover) {
+    pdl_entry();
     uint32_t ct = *ntasks;
     if (ct > task_cap) ct = task_cap;
     uint64_t nw = (uint64_t)gridDim.x * (blockDim.x / 32);
@@ -529,6 +551,7 @@ static __global__ void __launch_bounds__(256) k_finish_over(const uint64_t* __re
 // flight), and the four labels are written back only when one changed (after
 // the vertex-gathering pass most vertices already point at their root).
 static __global__ void k_finalize(UFState s, uint32_t* labels) {
+    pdl_entry();
     constexpr int W = 4;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
