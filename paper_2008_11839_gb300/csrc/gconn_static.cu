@@ -264,9 +264,10 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
     uint32_t* over = sc.over.as<uint32_t>();
     bool jtb = sv.link == GCONN_LINK_JTB;
     {
-        auto k = jtb ? k_vg<LK_JTB, true> : k_vg<LK_ASYNC, true>;
-        GC_TRY(launch_pdl("vg", k, grid_for(k, 256, (uint64_t)n), 256, 0, st, off, s, lmax, active, small, cnt + 0,
-                      tasks, (uint32_t)task_cap, cnt + 1, over, cnt + 2));
+        bool vec = !jtb && ((uintptr_t)off & 15u) == 0 && ((uintptr_t)s.P & 15u) == 0;
+        auto k = jtb ? k_vg<LK_JTB, true> : vec ? k_vg4<LK_ASYNC> : k_vg<LK_ASYNC, true>;
+        GC_TRY(launch_pdl("vg", k, grid_for(k, 256, vec ? ((uint64_t)n + 3) / 4 : (uint64_t)n), 256, 0, st, off, s,
+                          lmax, active, small, cnt + 0, tasks, (uint32_t)task_cap, cnt + 1, over, cnt + 2));
     }
     if (stats) {
         GC_CUDA(cudaEventRecord(stats->t_sampled, st));

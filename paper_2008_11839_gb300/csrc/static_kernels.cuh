@@ -385,6 +385,125 @@ static __global__ void __launch_bounds__(256) k_vg(const uint64_t* __restrict__ 
     }
 }
 
+// Vertex gathering with full compression for the min-linking rules, written
+// for few instructions per vertex: a warp takes 128 consecutive vertices, each
+// lane 4 of them, with one 16-byte parent load and two 16-byte offset loads
+// (the fifth offset is the next lane's first).  The lane's 4 root walks run in
+// lock step, changed parents go back in one 16-byte store, and the 4 active
+// bits of each lane are merged into the bitmask words by three shuffles.  The
+// list appends (rare after sampling) run only in warps that have active
+// vertices.  Needs 16-byte aligned offsets and parents; others use k_vg.
+template <int L>
+static __global__ void __launch_bounds__(256) k_vg4(const uint64_t* __restrict__ off, UFState s,
+                                                    const uint32_t* lmax_p, uint32_t* active, uint32_t* small,
+                                                    uint32_t* nsmall, unsigned long long* tasks, uint32_t task_cap,
+                                                    uint32_t* ntasks, uint32_t* over, uint32_t* nover) {
+    pdl_entry();
+    const uint32_t lmax = lmax_p ? *lmax_p : GC_DINF;
+    const uint64_t n = s.n;
+    const uint64_t nwords = (n + 31) / 32;
+    const uint64_t ngroups = (n + 127) / 128;
+    const unsigned lane = lane_id();
+    const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t gi = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; gi < ngroups; gi += nw) {
+        const uint64_t v0 = gi * 128 + 4 * (uint64_t)lane;
+        const bool full = v0 + 4 <= n;
+        uint32_t p[4];
+        uint64_t o[5];
+        if (full) {
+            uint4 pp = __ldca(reinterpret_cast<const uint4*>(s.P + v0));
+            ulonglong2 a = *reinterpret_cast<const ulonglong2*>(off + v0);
+            ulonglong2 b = *reinterpret_cast<const ulonglong2*>(off + v0 + 2);
+            p[0] = pp.x; p[1] = pp.y; p[2] = pp.z; p[3] = pp.w;
+            o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                bool in = v0 + j < n;
+                p[j] = in ? ldq<true>(s.P, (uint32_t)(v0 + j)) : 0u;   // vertex 0 is its own root
+                o[j] = v0 + j <= n ? off[v0 + j] : 0;                   // off[n] ends the last row
+            }
+        }
+        uint64_t nx = __shfl_down_sync(0xFFFFFFFFu, o[0], 1);   // next lane's off[v0 + 4]
+        if (lane == 31 || v0 + 4 >= n) nx = v0 + 4 <= n ? off[v0 + 4] : 0;
+        o[4] = nx;
+        uint32_t cur[4], nxt[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cur[j] = p[j];
+            nxt[j] = cur[j] < s.n ? ldq<true>(s.P, cur[j]) : cur[j];
+        }
+        for (uint32_t step = 0; step <= s.n; ++step) {
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (nxt[j] != cur[j]) {
+                    cur[j] = nxt[j];
+                    any = true;
+                }
+            }
+            if (!any) break;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) nxt[j] = cur[j] < s.n ? ldq<true>(s.P, cur[j]) : cur[j];
+            if (step == s.n) atomicOr(s.err, GC_DERR_NONCONV);
+        }
+        // P[v] = root(v)
+        bool changed = cur[0] != p[0] || cur[1] != p[1] || cur[2] != p[2] || cur[3] != p[3];
+        if (changed) {
+            if (full) {
+                __stcg(reinterpret_cast<uint4*>(s.P + v0), make_uint4(cur[0], cur[1], cur[2], cur[3]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (v0 + j < n && cur[j] != p[j]) stp(s.P, (uint32_t)(v0 + j), cur[j]);
+            }
+        }
+        unsigned nib = 0, snib = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint64_t deg = o[j + 1] - o[j];
+            bool act = v0 + j < n && deg > 0 && cur[j] != lmax;
+            nib |= (unsigned)act << j;
+            snib |= (unsigned)(act && deg <= (uint64_t)SMALL_DEG) << j;
+        }
+        if (active) {   // lane l holds bits 4(l % 8) .. 4(l % 8) + 3 of word 4 gi + l / 8
+            unsigned x = nib << (4 * (lane & 7));
+            x |= __shfl_xor_sync(0xFFFFFFFFu, x, 1);
+            x |= __shfl_xor_sync(0xFFFFFFFFu, x, 2);
+            x |= __shfl_xor_sync(0xFFFFFFFFu, x, 4);
+            uint64_t word = gi * 4 + lane / 8;
+            if ((lane & 7) == 0 && word < nwords) active[word] = x;
+        }
+        if (__any_sync(0xFFFFFFFFu, nib != 0)) {
+            unsigned c = __popc(snib), inc = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                unsigned t = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+                if ((int)lane >= d) inc += t;
+            }
+            unsigned total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+            uint32_t base = 0;
+            if (lane == 31 && total) base = atomicAdd(nsmall, total);
+            base = __shfl_sync(0xFFFFFFFFu, base, 31) + (inc - c);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if ((snib >> j) & 1u) small[base++] = (uint32_t)(v0 + j);
+                if (((nib & ~snib) >> j) & 1u) {
+                    uint64_t deg = o[j + 1] - o[j];
+                    uint64_t nch = (deg + TASK_ARCS - 1) / TASK_ARCS;
+                    uint32_t tb = atomicAdd(ntasks, (uint32_t)nch);
+                    if ((uint64_t)tb + nch <= task_cap) {
+                        for (uint64_t t = 0; t < nch; ++t)
+                            tasks[tb + t] = ((unsigned long long)(v0 + j) << 32) | t;
+                    } else {
+                        over[atomicAdd(nover, 1u)] = (uint32_t)(v0 + j);
+                    }
+                }
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ bool arc_needed(const uint32_t* active, uint32_t u, uint32_t v) {
     // each undirected edge is processed once: from its larger endpoint when
     // both are active, from the active one when the other was skipped
