@@ -291,13 +291,12 @@ static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_
     constexpr uint32_t SLOTS = 2 * LMAX_SAMPLES;
     __shared__ uint32_t key[SLOTS];
     __shared__ uint32_t cnt[SLOTS];
-    __shared__ unsigned long long best;
+    __shared__ unsigned long long wbest[LMAX_SAMPLES / 32];
     unsigned t = threadIdx.x;
     for (unsigned i = t; i < SLOTS; i += blockDim.x) {
         key[i] = GC_DINF;
         cnt[i] = 0;
     }
-    if (t == 0) best = 0;
     __syncthreads();
     uint32_t x = (uint32_t)(((uint64_t)hash_u32(seed, t) * s.n) >> 32);
     uint32_t lab = uf_root<L, true>(s, x);
@@ -316,14 +315,30 @@ static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_
         }
     }
     __syncthreads();
-    for (unsigned i = t; i < SLOTS; i += blockDim.x) {
+    // the best (count, label) key: larger count wins, on a tie the smaller
+    // label (larger ~label); a shuffle max per warp, then over the warps
+    unsigned long long mine = 0;
+    for (unsigned i = t; i < SLOTS; i += blockDim.x)
         if (cnt[i]) {
-            // larger count wins; on a tie the smaller label (larger ~label) wins
-            atomicMax(&best, ((unsigned long long)cnt[i] << 32) | (uint32_t)(~key[i]));
+            unsigned long long kv = ((unsigned long long)cnt[i] << 32) | (uint32_t)(~key[i]);
+            mine = kv > mine ? kv : mine;
         }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, mine, o);
+        mine = other > mine ? other : mine;
     }
+    if (lane_id() == 0) wbest[t / 32] = mine;
     __syncthreads();
-    if (t == 0) *lmax_out = ~(uint32_t)best;
+    if (t < 32) {
+        mine = t < LMAX_SAMPLES / 32 ? wbest[t] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, mine, o);
+            mine = other > mine ? other : mine;
+        }
+        if (t == 0) *lmax_out = ~(uint32_t)mine;
+    }
 }
 
 // Vertex gathering (the VG optimisation): vertices whose sampled label is not
