@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -323,6 +324,15 @@ def run_ours(args, rank, world, local_rank):
     step_share = {k: round(vv["ms"] / max(sum(x["ms"] for x in prof_all.values()), 1e-9), 4)
                   for k, vv in prof_all.items()}
     kernel_us = {k: round(1e3 * vv["ms"] / max(vv["launches"], 1), 2) for k, vv in prof_all.items()}
+    # whole-pass algorithmic bytes (the kernels that stream per-vertex data;
+    # after sampling the finish's active-set bytes are negligible) and the
+    # input-equivalent bandwidth (8m + 12n) / t, which sampling lets exceed HBM
+    pass_b = sum(alg_bytes(name, st) or 0 for name in prof_all)
+    pass_gbs = pass_b / (ms * 1e-3) / 1e9
+    pass_roof = {"alg_bytes": pass_b, "kernels": [x for x in prof_all if alg_bytes(x, st)],
+                 "achieved": round(pass_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(pass_gbs / hbm, 4)}
+    input_eq = {"value": round((8 * M + 12 * n) / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                "definition": "(8 m + 12 n) / step time: the bytes an unsampled pass would stream"}
 
     result = {"metric": "static CC edges/s (RMAT scale 22, 2^26 undirected edges)",
               "value": M * world / (ms * 1e-3), "unit": "edges/s", "n_gpus": world, "steps": args.steps,
@@ -335,7 +345,8 @@ def run_ours(args, rank, world, local_rank):
                          "variant": args.variant, "input": "CSR (u64 offsets, u32 cols), resident",
                          "launch": "one captured CUDA graph per step (gconn_plan_run)",
                          "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
-              "roofline": roof, "kernel_share": step_share, "kernel_us": kernel_us,
+              "roofline": roof, "pass_roofline": pass_roof, "input_equivalent_bw": input_eq,
+              "kernel_share": step_share, "kernel_us": kernel_us,
               "instrumentation": {"timed_region": f"events around {dom_name} only",
                                   "kernel_share": "separate replay loop, every kernel bracketed by events"},
               "clocks": clk,
@@ -368,6 +379,7 @@ def run_ours(args, rank, world, local_rank):
         result["serving"] = run_serving(g, torch, args)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(n, e, args.cpu_seconds)
+        result["cpu_multicore"] = cpu_multicore(n, M, off, cols, args.scale)
     if dist:
         dist.destroy_process_group()
     return result
@@ -376,25 +388,39 @@ def run_ours(args, rank, world, local_rank):
 def run_incremental(g, torch, dev, stream, args):
     """The insert/query stream on n = 2^24: 2^28 RMAT scale-24 insertions in
     batches of log-uniform size in [10^3, 10^8], each followed by a query
-    batch of the same size of uniform random pairs."""
+    batch of the same size of uniform random pairs.  Stream s of the
+    args.inc_seeds streams draws its own batch-size sequence and relabels the
+    vertices of the same edge multiset by its own seeded permutation (done on
+    the device, outside the timed batches), so per-batch latencies can be
+    pooled per batch-size decade; one extra pass of stream 0 warms up."""
     n = 1 << INC_N_SCALE
-    sizes = inc_batches(SEED_INC)
-    total = sum(sizes)
     perm = graphgen.permutation(n, SEED_INC, 6)
-    ins = torch.empty((total, 2), dtype=torch.int32, device=dev)
+    total = INC_TOTAL
+    ins0 = torch.empty((total, 2), dtype=torch.int32, device=dev)
     qry = torch.empty((total, 2), dtype=torch.int32, device=dev)
     chunk = 1 << 25
     buf = np.empty((chunk, 2), np.uint32)
     for s in range(0, total, chunk):
         c = min(chunk, total - s)
         graphgen.rmat_range(INC_N_SCALE, s, c, SEED_INC, perm=perm, out=buf[:c])
-        ins[s:s + c].copy_(torch.from_numpy(buf[:c].view(np.int32)))
+        ins0[s:s + c].copy_(torch.from_numpy(buf[:c].view(np.int32)))
         graphgen.pairs_range(n, s, c, SEED_INC, out=buf[:c])
         qry[s:s + c].copy_(torch.from_numpy(buf[:c].view(np.int32)))
+    ins = torch.empty_like(ins0)
     out = torch.empty(total, dtype=torch.uint8, device=dev)
     v = parse_variant(g, "none/" + args.inc_variant)
-    res = {}
-    for rep in range(2):                       # first pass warms up
+    recs = []                                   # (batch size, insert ms, query ms)
+    nseeds = max(1, args.inc_seeds)
+    for rep in range(nseeds + 1):               # rep 0 warms up on stream 0
+        si = max(rep - 1, 0)
+        sizes = inc_batches(SEED_INC + si)
+        if si == 0:
+            ins.copy_(ins0)
+        else:                                   # relabel: ins = pi_s[ins0], chunked
+            pi = torch.from_numpy(graphgen.permutation(n, SEED_INC + si, 7).view(np.int32)).to(dev).long()
+            for s in range(0, total, chunk):
+                ins[s:s + chunk] = pi[ins0[s:s + chunk].long()].int()
+            del pi
         inc = g.Incremental(n, v, stream)
         evs = []
         s = 0
@@ -410,20 +436,35 @@ def run_incremental(g, torch, dev, stream, args):
             s += b
         torch.cuda.synchronize()
         g.gconn_sync(stream)
-        ins_ms = [a.elapsed_time(b_) for (_, a, b_, _) in evs]
-        q_ms = [b_.elapsed_time(c) for (_, _, b_, c) in evs]
         inc.close()
-        res = {"n": n, "inserts": total, "queries": total, "batches": len(sizes),
-               "variant": args.inc_variant,
-               "updates_per_s": total / (sum(ins_ms) * 1e-3),
-               "queries_per_s": total / (sum(q_ms) * 1e-3),
-               "ops_per_s": 2 * total / ((sum(ins_ms) + sum(q_ms)) * 1e-3),
-               "insert_batch_ms_p50": round(pct(ins_ms, 50), 4), "insert_batch_ms_p99": round(pct(ins_ms, 99), 4),
-               "query_batch_ms_p50": round(pct(q_ms, 50), 4), "query_batch_ms_p99": round(pct(q_ms, 99), 4),
-               "batch_sizes_min_max": [min(sizes), max(sizes)],
-               "latency": "device time per batch, CUDA events on the launching stream",
-               "inputs": "resident in HBM"}
-    del ins, qry, out
+        if rep > 0:
+            recs += [(b, a.elapsed_time(b_), b_.elapsed_time(c)) for (b, a, b_, c) in evs]
+    ins_ms = [r[1] for r in recs]
+    q_ms = [r[2] for r in recs]
+    per_decade = {}
+    for d in range(3, 9):
+        sel = [r for r in recs if 10 ** d <= r[0] < 10 ** (d + 1)]
+        if sel:
+            per_decade[f"1e{d}"] = {"batches": len(sel),
+                                    "insert_ms_p50": round(pct([r[1] for r in sel], 50), 4),
+                                    "insert_ms_p99": round(pct([r[1] for r in sel], 99), 4),
+                                    "query_ms_p50": round(pct([r[2] for r in sel], 50), 4),
+                                    "query_ms_p99": round(pct([r[2] for r in sel], 99), 4)}
+    small = [r for r in recs if r[0] < 1000]
+    if small:
+        per_decade["<1e3 (truncated last batch)"] = {"batches": len(small)}
+    res = {"n": n, "inserts_per_stream": total, "queries_per_stream": total, "streams": nseeds,
+           "batches": len(recs), "variant": args.inc_variant,
+           "updates_per_s": nseeds * total / (sum(ins_ms) * 1e-3),
+           "queries_per_s": nseeds * total / (sum(q_ms) * 1e-3),
+           "ops_per_s": 2 * nseeds * total / ((sum(ins_ms) + sum(q_ms)) * 1e-3),
+           "insert_batch_ms_p50": round(pct(ins_ms, 50), 4), "insert_batch_ms_p99": round(pct(ins_ms, 99), 4),
+           "query_batch_ms_p50": round(pct(q_ms, 50), 4), "query_batch_ms_p99": round(pct(q_ms, 99), 4),
+           "per_batch_size_decade": per_decade,
+           "batch_sizes_min_max": [min(r[0] for r in recs), max(r[0] for r in recs)],
+           "latency": "device time per batch, CUDA events on the launching stream",
+           "inputs": "resident in HBM"}
+    del ins, ins0, qry, out
     torch.cuda.empty_cache()
     return res
 
@@ -568,6 +609,42 @@ def run_serving(g, torch, args):
             "inputs": "host memory (pageable), copied through the server's pinned staging"}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
+def cpu_multicore(n, m, off, cols, scale):
+    """The multicore CPU baseline (k-out sampling + lock-free union-find on all
+    host cores) on the whole graph; best of 3 runs."""
+    import cpu_baseline as cb
+    lab = np.empty(n, np.uint32)
+    cb.cc_csr(n, off, cols, out=lab)
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        cb.cc_csr(n, off, cols, out=lab)
+        ts.append(time.perf_counter() - t0)
+    dt = min(ts)
+    return {"value": m / dt, "unit": "edges/s", "cores": cb.max_threads(), "kind": "multicore baseline",
+            "method": "k-out (k=2) + L_max skip + lock-free Rem-CAS union-find, OpenMP",
+            "sample": f"whole RMAT s{scale} CSR ({n} vertices, {m} undirected edges), best of 3",
+            "ms": round(dt * 1e3, 3), "cpu_model": cpu_model()}
+
+
 def cpu_baseline(n, e, seconds):
     """The oracle (sequential union-find, one host core) on the first m_s
     edges of the same edge list, m_s sized for about `seconds` of work."""
@@ -583,7 +660,8 @@ def cpu_baseline(n, e, seconds):
         dt = time.perf_counter() - t0
     return {"value": m_s / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
             "sample": f"first {m_s} edges of the RMAT s22 COO list, all {n} vertices; O1 union-find incl. "
-                      f"min-id canonicalisation", "seconds": round(dt, 3), "host_cores_available": os.cpu_count()}
+                      f"min-id canonicalisation", "seconds": round(dt, 3), "host_cores_available": os.cpu_count(),
+            "oracle_threads": 1, "cpu_model": cpu_model()}
 
 
 # ------------------------------------------------------------ reference arm
@@ -741,6 +819,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default=DEFAULT_VARIANT)
     ap.add_argument("--inc-variant", default="early/naive", help="link/find[/splice] of the incremental handle")
+    ap.add_argument("--inc-seeds", type=int, default=8, help="independent insert/query streams (latency pooling)")
     ap.add_argument("--no-incremental", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
