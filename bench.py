@@ -42,6 +42,10 @@ INC_N_SCALE = 24
 INC_TOTAL = 1 << 28
 L2_FLUSH_BYTES = 256 << 20        # > 126 MB L2
 DEFAULT_VARIANT = "kout/remcas/naive/split_one"
+# DRAM bytes (read + write) of one k_kout launch per vertex, from an ncu capture
+# of the default variant at RMAT scale 20, edge factor 16 (42.34 MB / 2^20);
+# valid while that kernel is unchanged.
+KOUT_DRAM_BYTES_PER_VERTEX = 42.339e6 / 2 ** 20
 
 
 def parse_variant(g, spec: str):
@@ -318,9 +322,14 @@ def run_ours(args, rank, world, local_rank):
         b = alg_bytes(dom[0], st)
         if b is not None:
             ach = b / (per_launch_ms * 1e-3) / 1e9
+            traffic, tsrc = None, None
+            if dom[0] == "kout" and args.variant == DEFAULT_VARIANT and args.edges == 16 * n:
+                traffic = int(KOUT_DRAM_BYTES_PER_VERTEX * n)
+                tsrc = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_kout launch at RMAT scale 20 "
+                        "(same variant and edge factor), scaled by the vertex count")
             roof = {"kernel": dom[0], "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                    "frac": round(ach / hbm, 4), "traffic": None, "peak_source": peak_src,
-                    "alg_bytes_per_launch": b, "avg_launch_ms": round(per_launch_ms, 5)}
+                    "frac": round(ach / hbm, 4), "traffic": traffic, "traffic_source": tsrc,
+                    "peak_source": peak_src, "alg_bytes_per_launch": b, "avg_launch_ms": round(per_launch_ms, 5)}
     step_share = {k: round(vv["ms"] / max(sum(x["ms"] for x in prof_all.values()), 1e-9), 4)
                   for k, vv in prof_all.items()}
     kernel_us = {k: round(1e3 * vv["ms"] / max(vv["launches"], 1), 2) for k, vv in prof_all.items()}
@@ -400,10 +409,15 @@ def run_incremental(g, torch, dev, stream, args):
     qry = torch.empty((total, 2), dtype=torch.int32, device=dev)
     chunk = 1 << 25
     buf = np.empty((chunk, 2), np.uint32)
+    if args.inc_gen == "ba":    # growth stream: vertex v arrives with total / n edges to earlier vertices
+        ba = graphgen.ba(n, total // n, SEED_INC)
+        ins0.copy_(torch.from_numpy(ba.view(np.int32)))
+        del ba
     for s in range(0, total, chunk):
         c = min(chunk, total - s)
-        graphgen.rmat_range(INC_N_SCALE, s, c, SEED_INC, perm=perm, out=buf[:c])
-        ins0[s:s + c].copy_(torch.from_numpy(buf[:c].view(np.int32)))
+        if args.inc_gen != "ba":
+            graphgen.rmat_range(INC_N_SCALE, s, c, SEED_INC, perm=perm, out=buf[:c])
+            ins0[s:s + c].copy_(torch.from_numpy(buf[:c].view(np.int32)))
         graphgen.pairs_range(n, s, c, SEED_INC, out=buf[:c])
         qry[s:s + c].copy_(torch.from_numpy(buf[:c].view(np.int32)))
     ins = torch.empty_like(ins0)
@@ -453,7 +467,9 @@ def run_incremental(g, torch, dev, stream, args):
     small = [r for r in recs if r[0] < 1000]
     if small:
         per_decade["<1e3 (truncated last batch)"] = {"batches": len(small)}
-    res = {"n": n, "inserts_per_stream": total, "queries_per_stream": total, "streams": nseeds,
+    res = {"n": n, "generator": "Barabasi-Albert, d = %d" % (total // n) if args.inc_gen == "ba"
+           else "RMAT scale 24 (Graph500 a, b, c), relabelled",
+           "inserts_per_stream": total, "queries_per_stream": total, "streams": nseeds,
            "batches": len(recs), "variant": args.inc_variant,
            "updates_per_s": nseeds * total / (sum(ins_ms) * 1e-3),
            "queries_per_s": nseeds * total / (sum(q_ms) * 1e-3),
@@ -820,6 +836,8 @@ def main():
     ap.add_argument("--variant", default=DEFAULT_VARIANT)
     ap.add_argument("--inc-variant", default="early/naive", help="link/find[/splice] of the incremental handle")
     ap.add_argument("--inc-seeds", type=int, default=8, help="independent insert/query streams (latency pooling)")
+    ap.add_argument("--inc-gen", choices=["rmat", "ba"], default="rmat",
+                    help="insert-stream generator: RMAT (default) or Barabasi-Albert growth")
     ap.add_argument("--no-incremental", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

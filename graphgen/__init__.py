@@ -11,6 +11,7 @@ Table 2), which are public datasets and are not used here:
 * ``rmat``        RMAT / Graph500 Kronecker edges, optional random relabelling
 * ``grid_paths``  2D grid with random edge removal plus long permuted paths
 * ``batched``     thousands of small ER / RMAT graphs with local ids
+* ``ba``          Barabasi-Albert preferential attachment (streaming inputs)
 * ``csr``         symmetric CSR with sorted rows built from a COO list
 """
 from __future__ import annotations
@@ -59,6 +60,7 @@ def _load():
                 "gg_rmat": (None, [i32, u64, u32, u32, u32, u64, vp, vp]),
                 "gg_rmat_range": (None, [i32, u64, u64, u32, u32, u32, u64, vp, vp]),
                 "gg_pairs_range": (None, [u32, u64, u64, u64, vp]),
+                "gg_ba": (None, [u32, u32, u64, vp]),
                 "gg_shuffle_edges": (None, [u64, u64, u64, vp]),
                 "gg_grid_paths": (u64, [u32, u32, u32, u32, u64, vp]),
                 "gg_batched_sizes": (None, [u32, u32, u32, dbl, dbl, u64, vp, vp]),
@@ -137,6 +139,15 @@ def rmat_range(scale: int, start: int, count: int, seed: int, perm=None, abc=GRA
     ta, tab, tabc = _thresholds(abc)
     if count:
         _load().gg_rmat_range(scale, start, count, ta, tab, tabc, seed, _ptr(perm), _ptr(e))
+    return e
+
+
+def ba(n: int, d: int, seed: int, out=None) -> np.ndarray:
+    """Barabasi-Albert graph: vertex v attaches d edges (v, w), w <= v chosen
+    with probability proportional to degree (Batagelj-Brandes endpoint copying)."""
+    e = out_edges(n * d, out)
+    if n and d:
+        _load().gg_ba(n, d, seed, _ptr(e))
     return e
 
 

@@ -69,6 +69,24 @@ void gg_permutation(uint32_t n, uint64_t seed, uint64_t stream, uint32_t* perm) 
     }
 }
 
+/* Barabasi-Albert preferential attachment, d edges per new vertex, by the
+ * endpoint-copying method of Batagelj and Brandes ("Efficient generation of
+ * large random networks", Phys. Rev. E 71, 036113, 2005): the edge list itself
+ * is the list of all endpoints so far, and the far end of edge e (vertex
+ * v = e / d) is a uniformly chosen earlier entry, i.e. a vertex picked with
+ * probability proportional to its degree.  Entry 2e + 1 copies entry r, r
+ * uniform in [0, 2e] (r = 2e is v itself: a self-loop, kept, as are
+ * duplicates).  Draw e is output e of stream 9.  Sequential by nature. */
+void gg_ba(uint32_t n, uint32_t d, uint64_t seed, uint32_t* edges) {
+    uint64_t base = gg_stream(seed, 9);
+    uint64_t m = (uint64_t)n * d;
+    for (uint64_t e = 0; e < m; ++e) {
+        edges[2 * e] = (uint32_t)(e / d);
+        uint64_t r = (uint64_t)(((unsigned __int128)gg_at(base, e) * (2 * e + 1)) >> 64);
+        edges[2 * e + 1] = edges[r];
+    }
+}
+
 /* Erdos-Renyi G(n, m) multigraph: edge i has endpoints uniform in [0, n), drawn
  * from outputs 2i and 2i+1 of stream 1.  Self-loops and duplicates are kept. */
 void gg_er(uint32_t n, uint64_t m, uint64_t seed, uint32_t* edges) {

@@ -89,3 +89,27 @@ def test_csr_roundtrip():
     for v in range(0, n, 97):
         r = cols[off[v]:off[v + 1]]
         assert (np.diff(r.astype(np.int64)) >= 0).all()
+
+
+def test_ba_endpoint_copying_and_shape():
+    """Barabasi-Albert by Batagelj-Brandes endpoint copying: edge e starts at
+    e // d, its far end copies a uniformly drawn earlier endpoint (so it is an
+    earlier-or-same vertex), and the degree distribution is heavy-tailed."""
+    n, d, seed = 2000, 3, 41
+    e = graphgen.ba(n, d, seed)
+    m = n * d
+    assert e.shape == (m, 2)
+    assert (e[:, 0] == np.arange(m) // d).all()
+    assert (e[:, 1] <= e[:, 0]).all()
+    # the copying rule, restated from the published method on the same draws
+    h = graphgen.hash_fill(seed, 9, 0, m)
+    flat = np.empty(2 * m, np.int64)
+    for i in range(m):
+        flat[2 * i] = i // d
+        r = (int(h[i]) * (2 * i + 1)) >> 64
+        flat[2 * i + 1] = flat[r]
+    assert (flat.reshape(m, 2) == e).all()
+    assert (graphgen.ba(n, d, seed) == e).all() and not (graphgen.ba(n, d, seed + 1) == e).all()
+    big = graphgen.ba(100_000, 4, 5)
+    deg = np.bincount(big.ravel(), minlength=100_000)
+    assert deg.max() > 20 * deg.mean()          # hubs: early vertices gather ~ d sqrt(n / i) edges
