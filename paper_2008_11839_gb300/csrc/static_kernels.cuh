@@ -603,16 +603,21 @@ __global__ void __launch_bounds__(256) k_finish(const uint64_t* __restrict__ off
             uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
         }
     }
-    // low-degree vertices, flattened per warp: 32 listed vertices' arcs form one
+    // low-degree vertices, flattened per warp: G listed vertices' arcs form one
     // range [0, total) that the lanes cover densely (owner lane found by a
-    // shuffle binary search over the inclusive degree scan)
+    // shuffle binary search over the inclusive degree scan).  G is sized to the
+    // list: a short list (the usual case after sampling) is spread one vertex
+    // per warp, so no warp walks several rows' unions in sequence; a long one
+    // packs up to 32 vertices per warp.
     uint32_t cs = *nsmall;
-    for (uint64_t base = gw * 32; base < cs; base += nw * 32) {
+    uint64_t G = ((uint64_t)cs + nw - 1) / nw;
+    G = G < 1 ? 1 : G > 32 ? 32 : G;
+    for (uint64_t base = gw * G; base < cs; base += nw * G) {
         if (err_abort(s.err)) return;
         uint64_t i = base + lane;
         uint32_t u = 0, d = 0;
         uint64_t lo = 0;
-        if (i < cs) {
+        if (lane < G && i < cs) {
             u = small[i];
             lo = off[u];
             d = (uint32_t)(off[u + 1] - lo);
