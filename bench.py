@@ -384,6 +384,8 @@ def run_ours(args, rank, world, local_rank):
         result["incremental"] = run_incremental(g, torch, dev, stream, args)
     if rank == 0 and not args.no_batched:
         result["batched"] = run_batched(g, torch, dev, stream, args)
+    if rank == 0 and not args.no_forest:
+        result["spanning_forest"] = run_forest(g, torch, dev, stream, args, n, M, d_off, d_cols, labels, flush)
     if rank == 0 and not args.no_serving:
         result["serving"] = run_serving(g, torch, args)
     if rank == 0 and not args.no_cpu_baseline:
@@ -483,6 +485,36 @@ def run_incremental(g, torch, dev, stream, args):
     del ins, ins0, qry, out
     torch.cuda.empty_cache()
     return res
+
+
+def run_forest(g, torch, dev, stream, args, n, M, d_off, d_cols, labels, flush):
+    """Spanning forest (Algorithm 2) of the same RMAT graph through
+    gconn_spanning_forest_csr with device buffers; the forest must have
+    n - c edges (c = components of the timed CC pass)."""
+    v = parse_variant(g, args.variant)
+    forest = torch.empty(n, dtype=torch.int64, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    for i in range(args.warmup):
+        flush.fill_(i)
+        g.gconn_spanning_forest_csr(n, d_off, d_cols, forest, count, None, v, stream)
+    g.gconn_sync(stream)
+    ts = []
+    for i in range(args.steps):
+        flush.fill_(i + 700)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.gconn_spanning_forest_csr(n, d_off, d_cols, forest, count, None, v, stream)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    g.gconn_sync(stream)
+    comps = int(torch.unique(labels).numel())
+    cnt = int(count.item())
+    ms = float(np.mean(ts))
+    return {"edges_per_s": M / (ms * 1e-3), "ms": round(ms, 5), "ms_median": round(float(np.median(ts)), 5),
+            "forest_edges": cnt, "components": comps, "count_is_n_minus_c": cnt == n - comps,
+            "variant": args.variant, "output": "arc positions of the forest edges (int64), compacted on device",
+            "launch": "one C-ABI call per pass (stream-ordered, not a captured plan)"}
 
 
 def run_batched(g, torch, dev, stream, args):
@@ -842,6 +874,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-forest", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-edges", type=int, default=M_EDGES)
