@@ -159,6 +159,32 @@ def test_host_pointers_match():
     assert oracle.sf_check(n, e, forest[: int(cnt[0])], REF[name]) == 0
 
 
+@pytest.mark.parametrize("shape", ["rmat", "star", "ragged"])
+def test_large_host_csr_inputs(shape):
+    """Host (staged) CSR inputs with >= 8 Mi arcs and extreme row layouts (one
+    row holding every arc, a huge row amid isolated stretches, self-loops)
+    give exact labels."""
+    if shape == "rmat":
+        n = 1 << 19
+        e = graphgen.rmat(19, 1 << 23, 21)
+    elif shape == "star":          # one row holds every arc
+        n = 1 << 20
+        e = np.stack([np.zeros(1 << 22, np.uint32), graphgen.er(n, 1 << 22, 22)[:, 1]], axis=1)
+    else:                          # isolated stretches, a huge row in the middle, self-loops
+        n = (1 << 20) + 37
+        e = graphgen.er(n, 1 << 22, 23)
+        e[: 1 << 21, 0] = np.uint32(n // 2)
+        e[-1000:, 1] = e[-1000:, 0]
+    off, cols = graphgen.csr(n, e)
+    assert off[-1] >= 1 << 23
+    ref = oracle.cc_uf(n, e)
+    for spec in ("kout/remcas/naive/split_one", "kout/async/naive/none", "kout/early/halve/none"):
+        s, l, f, sp = spec.split("/")
+        lab = np.empty(n, np.uint32)
+        g.gconn_cc_csr(n, off, cols, lab, g.make_variant(sample=s, link=l, find=f, splice=sp))
+        assert (lab == ref).all(), spec
+
+
 def test_release_cached_then_rerun():
     """Scratch memory is cached between calls; releasing it leaves later calls exact."""
     import torch
