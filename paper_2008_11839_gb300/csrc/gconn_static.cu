@@ -149,7 +149,7 @@ struct CsrScratch {
 };
 
 gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,
-                        uint32_t* lmax_dev, unsigned long long* dq_count, cudaStream_t st) {
+                        uint32_t* lmax_dev, unsigned long long* dq_count, uint32_t* lmax_done, cudaStream_t st) {
     uint32_t n = s.n;
     int L, F, S;
     uf_triple(v, &L, &F, &S);
@@ -166,8 +166,11 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off,
             auto k = k_kout<l, f, sp, w>;
             GC_TRY(launch_pdl("kout", k, grid_for(k, KOUT_BLOCK, n), KOUT_BLOCK, 0, st, off, cols, v.k, s, dq));
             auto kj = k_union_jobs<l, f, sp, w>;
-            return launch_pdl("kout_deferred", kj, grid_for(kj, 256, qcap), 256, 0, st, s, dq);
+            // the last block of the retry kernel also computes L_max
+            return launch_pdl("kout_deferred", kj, grid_for(kj, LMAX_SAMPLES, qcap), LMAX_SAMPLES, 0, st, s, dq,
+                              v.seed, lmax_dev, lmax_done);
         }));
+        return GCONN_OK;
     } else if (v.sample == GCONN_SAMPLE_HB) {
         GC_TRY(launch("hb1", k_hb1, grid_for(k_hb1, 256, n), 256, 0, st, off, cols, n, s.P, s.sf, s.err));
         if (jtb) {
@@ -237,7 +240,8 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
     CsrScratch sc;
     bool sampled = v.sample != GCONN_SAMPLE_NONE;
     // the pass's counters in one 64-byte header, cleared by the init kernel:
-    // [0] L_max, [1..3] gathering counters, [8..9] deferred-union count (u64)
+    // [0] L_max, [1..3] gathering counters, [8..9] deferred-union count (u64),
+    // [10] blocks of the retry kernel done (the last one computes L_max)
     GC_TRY(sc.counters.alloc(16 * sizeof(uint32_t), st));
     uint32_t* hdr = sc.counters.as<uint32_t>();
     uint32_t* lmax = sampled ? hdr : nullptr;
@@ -248,7 +252,7 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
     Variant sv = v;
     bool rounds = is_rounds_link(v.link);
     if (rounds) { sv.link = GCONN_LINK_ASYNC; sv.find = GCONN_FIND_NAIVE; sv.splice = 0; }
-    if (sampled) GC_TRY(csr_sample(sv, s, off, cols, lmax, dq_count, st));
+    if (sampled) GC_TRY(csr_sample(sv, s, off, cols, lmax, dq_count, hdr + 10, st));
     // vertex gathering
     uint64_t task_cap = (uint64_t)n + 1024;
     uint32_t* active = nullptr;

@@ -200,9 +200,90 @@ static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __re
     }
 }
 
+// GetMostFrequentLabel (Algorithm 1): mode of the root labels of
+// LMAX_SAMPLES seeded random vertices, ties to the smaller label.  A block of
+// any size (a multiple of 32) walks the samples to their roots (thread t takes
+// samples t, t + blockDim, ...) and counts them in a shared-memory
+// open-addressing table; the best (count, smallest label) wins.  L1 selects
+// L1-allowed parent loads (only safe in a kernel that has not itself changed P).
+constexpr uint32_t LMAX_SLOTS = 2 * LMAX_SAMPLES;
+
+struct LmaxSmem {
+    uint32_t key[LMAX_SLOTS];
+    uint32_t cnt[LMAX_SLOTS];
+    unsigned long long wbest[32];
+};
+
+template <int L, bool L1>
+__device__ void block_lmax(const UFState& s, uint64_t seed, uint32_t* lmax_out, LmaxSmem& sm) {
+    const unsigned t = threadIdx.x, nt = blockDim.x;
+    for (unsigned i = t; i < LMAX_SLOTS; i += nt) {
+        sm.key[i] = GC_DINF;
+        sm.cnt[i] = 0;
+    }
+    __syncthreads();
+    for (unsigned j = t; j < LMAX_SAMPLES; j += nt) {   // every lane of a warp runs the same iterations
+        uint32_t x = (uint32_t)(((uint64_t)hash_u32(seed, j) * s.n) >> 32);
+        uint32_t lab = uf_root<L, L1>(s, x);
+        // lanes holding the same label add it once (the big component's label
+        // would otherwise serialise hundreds of shared-memory atomics)
+        unsigned peers = __match_any_sync(0xFFFFFFFFu, lab);
+        if ((unsigned)(__ffs(peers) - 1) == lane_id()) {
+            uint32_t slot = hash_u32(0x5A17ull, lab) & (LMAX_SLOTS - 1);
+            for (uint32_t probe = 0; probe < LMAX_SLOTS; ++probe) {
+                uint32_t prev = atomicCAS(&sm.key[slot], GC_DINF, lab);
+                if (prev == GC_DINF || prev == lab) {
+                    atomicAdd(&sm.cnt[slot], (uint32_t)__popc(peers));
+                    break;
+                }
+                slot = (slot + 1) & (LMAX_SLOTS - 1);
+            }
+        }
+    }
+    __syncthreads();
+    // larger count wins, on a tie the smaller label (larger ~label): a
+    // shuffle max per warp, then over the warps
+    unsigned long long mine = 0;
+    for (unsigned i = t; i < LMAX_SLOTS; i += nt)
+        if (sm.cnt[i]) {
+            unsigned long long kv = ((unsigned long long)sm.cnt[i] << 32) | (uint32_t)(~sm.key[i]);
+            mine = kv > mine ? kv : mine;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, mine, o);
+        mine = other > mine ? other : mine;
+    }
+    if (lane_id() == 0) sm.wbest[t / 32] = mine;
+    __syncthreads();
+    if (t < 32) {
+        mine = t < nt / 32 ? sm.wbest[t] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, mine, o);
+            mine = other > mine ? other : mine;
+        }
+        if (t == 0) *lmax_out = ~(uint32_t)mine;
+    }
+}
+
+template <int L>
+static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_t seed, uint32_t* lmax_out) {
+    pdl_entry();
+    __shared__ LmaxSmem sm;
+    block_lmax<L, true>(s, seed, lmax_out, sm);
+}
+
 // Unions deferred by k_kout, re-run from their endpoints with the full cap.
+// Blocks of LMAX_SAMPLES threads.  With lmax_out set, the block that finishes
+// last (a counter taken after a fence; `done` must start at zero) also
+// computes L_max, one sample per thread, which needs every
+// union done: no block waits for another, the last one just does more work.
+// It reads parents through L2 only, since its own L1 may hold lines from
+// before other blocks' links.
 template <int L, int F, int S, bool SF>
-static __global__ void __launch_bounds__(256) k_union_jobs(UFState s, JobQueue dq) {
+static __global__ void __launch_bounds__(LMAX_SAMPLES) k_union_jobs(UFState s, JobQueue dq, uint64_t seed,
+                                                           uint32_t* lmax_out, uint32_t* done) {
     pdl_entry();
     unsigned long long cnt = *dq.count;
     if (cnt > dq.cap) cnt = dq.cap;
@@ -212,6 +293,16 @@ static __global__ void __launch_bounds__(256) k_union_jobs(UFState s, JobQueue d
         Spin sp(s.cap);
         uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
     }
+    if (!lmax_out) return;
+    __shared__ LmaxSmem sm;
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    block_lmax<L == LK_JTB ? LK_JTB : LK_ASYNC, false>(s, seed, lmax_out, sm);
 }
 
 // HB sampling step 1 (Algorithm 3): P[v] = min(v, w) for the smallest
@@ -281,65 +372,6 @@ static __global__ void k_w_from_p(uint32_t n, const uint32_t* P, u64w* W) {
     }
 }
 
-// GetMostFrequentLabel (Algorithm 1): mode of the root labels of
-// LMAX_SAMPLES seeded random vertices, ties to the smaller label.  One block:
-// each thread walks its sample to the root and counts it in a shared-memory
-// open-addressing table; the best (count, smallest label) wins.
-template <int L>
-static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_t seed, uint32_t* lmax_out) {
-    pdl_entry();
-    constexpr uint32_t SLOTS = 2 * LMAX_SAMPLES;
-    __shared__ uint32_t key[SLOTS];
-    __shared__ uint32_t cnt[SLOTS];
-    __shared__ unsigned long long wbest[LMAX_SAMPLES / 32];
-    unsigned t = threadIdx.x;
-    for (unsigned i = t; i < SLOTS; i += blockDim.x) {
-        key[i] = GC_DINF;
-        cnt[i] = 0;
-    }
-    __syncthreads();
-    uint32_t x = (uint32_t)(((uint64_t)hash_u32(seed, t) * s.n) >> 32);
-    uint32_t lab = uf_root<L, true>(s, x);
-    // lanes holding the same label add it once (the big component's label
-    // would otherwise serialise hundreds of shared-memory atomics)
-    unsigned peers = __match_any_sync(0xFFFFFFFFu, lab);
-    if ((unsigned)(__ffs(peers) - 1) == lane_id()) {
-        uint32_t slot = hash_u32(0x5A17ull, lab) & (SLOTS - 1);
-        for (uint32_t probe = 0; probe < SLOTS; ++probe) {
-            uint32_t prev = atomicCAS(&key[slot], GC_DINF, lab);
-            if (prev == GC_DINF || prev == lab) {
-                atomicAdd(&cnt[slot], (uint32_t)__popc(peers));
-                break;
-            }
-            slot = (slot + 1) & (SLOTS - 1);
-        }
-    }
-    __syncthreads();
-    // the best (count, label) key: larger count wins, on a tie the smaller
-    // label (larger ~label); a shuffle max per warp, then over the warps
-    unsigned long long mine = 0;
-    for (unsigned i = t; i < SLOTS; i += blockDim.x)
-        if (cnt[i]) {
-            unsigned long long kv = ((unsigned long long)cnt[i] << 32) | (uint32_t)(~key[i]);
-            mine = kv > mine ? kv : mine;
-        }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, mine, o);
-        mine = other > mine ? other : mine;
-    }
-    if (lane_id() == 0) wbest[t / 32] = mine;
-    __syncthreads();
-    if (t < 32) {
-        mine = t < LMAX_SAMPLES / 32 ? wbest[t] : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, mine, o);
-            mine = other > mine ? other : mine;
-        }
-        if (t == 0) *lmax_out = ~(uint32_t)mine;
-    }
-}
 
 // Vertex gathering (the VG optimisation): vertices whose sampled label is not
 // L_max and that have edges become active.  Low-degree ones go to a list
