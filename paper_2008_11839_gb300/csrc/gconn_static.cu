@@ -233,8 +233,10 @@ static __global__ void k_sample_stats(const uint64_t* __restrict__ off, const ui
     atomicAdd(c + 5, insp);
 }
 
+// With `finalized` non-null, a union-find finish also finalises the labels in
+// P (from the gathered lists, k_finalize_gathered) and sets *finalized.
 gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,
-                         cudaStream_t st, CsrStats* stats = nullptr) {
+                         cudaStream_t st, CsrStats* stats = nullptr, bool* finalized = nullptr) {
     uint32_t n = s.n;
     if (n == 0) return GCONN_OK;
     CsrScratch sc;
@@ -286,13 +288,21 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
     int L, F, S;
     uf_triple(v, &L, &F, &S);
     int B = block_of(v);
-    return dispatch_uf(L, F, S, s.sf != nullptr, [&]<int l, int f, int sp, bool w>() {
+    GC_TRY(dispatch_uf(L, F, S, s.sf != nullptr, [&]<int l, int f, int sp, bool w>() {
         auto k = k_finish<l, f, sp, w>;
         return launch_pdl("finish", k, grid_for(k, B, (uint64_t)n * 32), B, 0, st, off, cols, s,
                       (const uint32_t*)active, (const uint32_t*)small, (const uint32_t*)(cnt + 0),
                       (const unsigned long long*)tasks, (const uint32_t*)(cnt + 1), (uint32_t)task_cap,
                       (const uint32_t*)over, (const uint32_t*)(cnt + 2));
-    });
+    }));
+    if (finalized && !jtb) {   // the lists are freed with this call's scratch: finalise now
+        GC_TRY(launch_pdl("finalize", k_finalize_gathered, grid_for(k_finalize_gathered, 256, n), 256, 0, st, s,
+                          (const uint32_t*)lmax, (const uint32_t*)small, (const uint32_t*)(cnt + 0),
+                          (const unsigned long long*)tasks, (const uint32_t*)(cnt + 1), (uint32_t)task_cap,
+                          (const uint32_t*)over, (const uint32_t*)(cnt + 2)));
+        *finalized = true;
+    }
+    return GCONN_OK;
 }
 
 // --------------------------------------------------------------- drivers
@@ -404,12 +414,12 @@ static gconn_status static_run(uint32_t n, uint64_t m, const uint32_t* edges, co
         } else {
             GC_TRY(union_coo(v, s, d_edges, m, 0, st));
         }
-    } else {
-        GC_TRY(csr_connect(v, s, d_off, d_cols, st));
     }
+    bool finalized = false;
+    if (csr) GC_TRY(csr_connect(v, s, d_off, d_cols, st, nullptr, labels ? &finalized : nullptr));
     if (labels) {
         // rounds-based finishes leave P fully compressed and min-rooted
-        GC_TRY(finalize_labels(v, s, P, st));
+        if (!finalized) GC_TRY(finalize_labels(v, s, P, st));
         if (labels_host) GC_CUDA(cudaMemcpyAsync(labels, P, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
     }
     if (want_forest) {
@@ -462,8 +472,9 @@ extern "C" gconn_status gconn_cc_csr_stats(uint32_t n, const uint64_t* offsets, 
     cudaEventCreate(&e2);
     CsrStats cs{cb.as<unsigned long long>(), e1, e1b, (uint32_t*)(cb.as<unsigned long long>() + 8)};
     GC_CUDA(cudaEventRecord(e0, st));
-    gconn_status r = csr_connect(v, s, offsets, cols, st, &cs);
-    if (r == GCONN_OK) r = finalize_labels(v, s, labels, st);
+    bool finalized = false;
+    gconn_status r = csr_connect(v, s, offsets, cols, st, &cs, &finalized);
+    if (r == GCONN_OK && !finalized) r = finalize_labels(v, s, labels, st);
     if (r == GCONN_OK) r = cuda_status(cudaEventRecord(e2, st));
     unsigned long long h[8] = {0};
     if (r == GCONN_OK) r = cuda_status(cudaMemcpyAsync(h, cb.p, sizeof(h), cudaMemcpyDeviceToHost, st));

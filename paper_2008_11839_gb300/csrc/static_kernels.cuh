@@ -721,8 +721,7 @@ static __global__ void __launch_bounds__(256) k_finish_over(const uint64_t* __re
 // with one 16-byte load; the four walks advance in lock step (four parent loads in
 // flight), and the four labels are written back only when one changed (after
 // the vertex-gathering pass most vertices already point at their root).
-static __global__ void k_finalize(UFState s, uint32_t* labels) {
-    pdl_entry();
+__device__ __forceinline__ void finalize_all(const UFState& s, uint32_t* labels) {
     constexpr int W = 4;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -751,6 +750,39 @@ static __global__ void k_finalize(UFState s, uint32_t* labels) {
             reinterpret_cast<uint4*>(labels)[q] = make_uint4(cur[0], cur[1], cur[2], cur[3]);
     }
     for (uint64_t v = nv * 4 + t0; v < s.n; v += stride) labels[v] = uf_root<LK_ASYNC, true>(s, (uint32_t)v);
+}
+
+static __global__ void k_finalize(UFState s, uint32_t* labels) {
+    pdl_entry();
+    finalize_all(s, labels);
+}
+
+// LabelFinalization in place after vertex gathering.  Gathering left every
+// vertex pointing at its sampled root, and a root moves in the finish only
+// when a union links it: the roots of active components (whose vertices all
+// have edges and a label other than L_max, so all of them are in the gathered
+// lists) or the L_max root itself.  So while P[L_max] is still L_max, walking
+// the listed vertices to their roots finalises every label; otherwise (or
+// without an L_max) every vertex is walked.
+static __global__ void k_finalize_gathered(UFState s, const uint32_t* lmax_p, const uint32_t* small,
+                                           const uint32_t* nsmall, const unsigned long long* tasks,
+                                           const uint32_t* ntasks, uint32_t task_cap, const uint32_t* over,
+                                           const uint32_t* nover) {
+    pdl_entry();
+    uint32_t lmax = lmax_p ? *lmax_p : GC_DINF;
+    if (lmax >= s.n || ldp(s.P, lmax) != lmax) {
+        finalize_all(s, s.P);
+        return;
+    }
+    uint64_t cs = *nsmall, ct = *ntasks, co = *nover;
+    if (ct > task_cap) ct = task_cap;
+    uint64_t total = cs + ct + co;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        uint32_t u = i < cs ? small[i] : i < cs + ct ? (uint32_t)(tasks[i - cs] >> 32) : over[i - cs - ct];
+        uint32_t r = uf_root<LK_ASYNC, true>(s, u);
+        if (ldp(s.P, u) != r) stp(s.P, u, r);
+    }
 }
 
 // Union-JTB roots are not minimal: canonicalise through the root.
