@@ -30,6 +30,7 @@ constexpr uint32_t SMEM_MAX_N = 65536;
 constexpr uint32_t SMEM_CAP = 1u << 20;   // loop cap per shared-memory union
 
 enum { BR_ASYNC_NAIVE = 0, BR_ASYNC_HALVE = 1, BR_REM_SPLIT = 2 };
+constexpr int BATCH_ILP = 8;   // edge loads in flight per thread
 
 __device__ __forceinline__ uint32_t sm_ld(const volatile uint16_t* P, uint32_t i) { return P[i]; }
 __device__ __forceinline__ uint32_t sm_cas(volatile uint16_t* P, uint32_t i, uint32_t cmp, uint32_t val) {
@@ -111,14 +112,23 @@ __global__ void k_batch_smem(const uint64_t* __restrict__ vo, const uint64_t* __
         uint64_t eb = eo[g], m = eo[g + 1] - eb;
         for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) P[i] = (uint16_t)i;
         __syncthreads();
-        for (uint64_t j = threadIdx.x; j < m; j += blockDim.x) {
-            uint2 e = __ldcs(E + eb + j);
-            if (e.x >= n || e.y >= n) {
-                atomicOr(err, GC_DERR_RANGE);
-                continue;
-            }
-            if (e.x != e.y) sm_union<R>(P, e.x, e.y, err);
+        // BATCH_ILP coalesced edge loads in flight per thread before their
+        // unions: the edge stream, not the shared-memory unions, is the
+        // latency that bounds a large graph's CTA
+        auto one = [&](uint2 e) {
+            if (e.x >= n || e.y >= n) atomicOr(err, GC_DERR_RANGE);
+            else if (e.x != e.y) sm_union<R>(P, e.x, e.y, err);
+        };
+        const uint64_t B = blockDim.x;
+        uint64_t j = threadIdx.x;
+        for (; j + (BATCH_ILP - 1) * B < m; j += BATCH_ILP * B) {
+            uint2 e[BATCH_ILP];
+#pragma unroll
+            for (int q = 0; q < BATCH_ILP; ++q) e[q] = __ldcs(E + eb + j + q * B);
+#pragma unroll
+            for (int q = 0; q < BATCH_ILP; ++q) one(e[q]);
         }
+        for (; j < m; j += B) one(__ldcs(E + eb + j));
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
             uint32_t r = i, left = SMEM_CAP;
