@@ -284,6 +284,11 @@ gconn_status gconn_plan_create_cc(uint32_t n, uint64_t m, const uint32_t* edges,
                                   const gconn_variant* v, gconn_plan** out);
 gconn_status gconn_plan_create_cc_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
                                       uint32_t* labels, const gconn_variant* v, gconn_plan** out);
+/* The spanning-forest pass of gconn_spanning_forest_csr (Algorithm 2) as a
+ * plan: forest, forest_count and (optional) labels must be device memory. */
+gconn_status gconn_plan_create_forest_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
+                                          uint64_t* forest, uint64_t* forest_count, uint32_t* labels,
+                                          const gconn_variant* v, gconn_plan** out);
 gconn_status gconn_plan_run(gconn_plan* p, void* stream);
 gconn_status gconn_plan_destroy(gconn_plan* p);
 

@@ -140,6 +140,8 @@ _SIGS = {
     "gconn_batch_autotune": (_i32, [_u32, _vp, _vp, _vp, _vp, ctypes.POINTER(gconn_batch_tune), _vp]),
     "gconn_plan_create_cc": (_i32, [_u32, _u64, _vp, _vp, ctypes.POINTER(gconn_variant), ctypes.POINTER(_vp)]),
     "gconn_plan_create_cc_csr": (_i32, [_u32, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), ctypes.POINTER(_vp)]),
+    "gconn_plan_create_forest_csr": (_i32, [_u32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(gconn_variant),
+                                            ctypes.POINTER(_vp)]),
     "gconn_plan_run": (_i32, [_vp, _vp]),
     "gconn_plan_destroy": (_i32, [_vp]),
     "gconn_profile_sync": (_i32, []),
@@ -356,6 +358,13 @@ def gconn_plan_create_cc_csr(n, offsets, cols, labels, variant=None):
     h = ctypes.c_void_p()
     check(lib().gconn_plan_create_cc_csr(n, ptr(offsets), ptr(cols), ptr(labels), _vref(variant), ctypes.byref(h)),
           "gconn_plan_create_cc_csr")
+    return h
+
+
+def gconn_plan_create_forest_csr(n, offsets, cols, forest, forest_count, labels=None, variant=None):
+    h = ctypes.c_void_p()
+    check(lib().gconn_plan_create_forest_csr(n, ptr(offsets), ptr(cols), ptr(forest), ptr(forest_count), ptr(labels),
+                                             _vref(variant), ctypes.byref(h)), "gconn_plan_create_forest_csr")
     return h
 
 

@@ -55,9 +55,9 @@ gconn_status capture_plan(Body&& body, gconn_plan** out) {
     return GCONN_OK;
 }
 
-gconn_status plan_variant_ok(const gconn_variant* vin, int input_kind) {
+gconn_status plan_variant_ok(const gconn_variant* vin, int input_kind, int want_forest = 0) {
     Variant v;
-    GC_TRY(resolve_variant(vin, input_kind, 0, &v));
+    GC_TRY(resolve_variant(vin, input_kind, want_forest, &v));
     if (v.sample == GCONN_SAMPLE_BFS || is_rounds_link(v.link))
         return GCONN_E_UNSUPPORTED;   // these read a device flag on the host every round
     return GCONN_OK;
@@ -82,6 +82,20 @@ extern "C" gconn_status gconn_plan_create_cc_csr(uint32_t n, const uint64_t* off
         return GCONN_E_INVAL;
     GC_TRY(plan_variant_ok(v, 1));
     return capture_plan([&](cudaStream_t st) { return gconn_cc_csr(n, offsets, cols, labels, v, st); }, out);
+}
+
+extern "C" gconn_status gconn_plan_create_forest_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
+                                                     uint64_t* forest, uint64_t* forest_count, uint32_t* labels,
+                                                     const gconn_variant* v, gconn_plan** out) {
+    if (!out) return GCONN_E_INVAL;
+    *out = nullptr;
+    if (!offsets || !cols || !forest || !forest_count || !is_device_ptr(offsets) || !is_device_ptr(cols) ||
+        !is_device_ptr(forest) || !is_device_ptr(forest_count) || (labels && !is_device_ptr(labels)))
+        return GCONN_E_INVAL;
+    GC_TRY(plan_variant_ok(v, 1, 1));
+    return capture_plan([&](cudaStream_t st) {
+        return gconn_spanning_forest_csr(n, offsets, cols, forest, forest_count, labels, v, st);
+    }, out);
 }
 
 extern "C" gconn_status gconn_plan_run(gconn_plan* p, void* stream) {

@@ -807,21 +807,45 @@ static __global__ void k_jtb_gather(UFState s, uint32_t* labels) {
 }
 
 // Spanning forest output: compact the recorded slots into a dense id list.
-static __global__ void k_sf_compact(uint32_t n, const uint32_t* sf, unsigned long long* out, unsigned long long* count) {
-    uint64_t nwords = ((uint64_t)n + 31) / 32;
-    uint64_t wstride = (uint64_t)gridDim.x * (blockDim.x / 32);
-    unsigned lane = lane_id();
-    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nwords; w += wstride) {
+static __global__ void __launch_bounds__(256) k_sf_compact(uint32_t n, const uint32_t* sf, unsigned long long* out,
+                                                            unsigned long long* count) {
+    // Each block owns a contiguous range of 32-vertex words and reserves its
+    // output slots with ONE atomic: pass 1 counts (ballots), pass 2 re-reads
+    // the same words in the same order and writes (one counter shared by
+    // thousands of per-warp atomics would serialise at its L2 slice).
+    __shared__ unsigned long long wsum[8];
+    __shared__ unsigned long long base;
+    const uint64_t nwords = ((uint64_t)n + 31) / 32;
+    const uint64_t per = (nwords + gridDim.x - 1) / gridDim.x;
+    const uint64_t w0 = (uint64_t)blockIdx.x * per;
+    const uint64_t w1 = w0 + per < nwords ? w0 + per : nwords;
+    const unsigned lane = lane_id(), warp = threadIdx.x / 32, nwarp = blockDim.x / 32;
+    unsigned long long mine = 0;
+    for (uint64_t w = w0 + warp; w < w1; w += nwarp) {
+        uint64_t v = w * 32 + lane;
+        bool has = v < n && sf[v] != GC_DINF;
+        mine += __popc(__ballot_sync(0xFFFFFFFFu, has));
+    }
+    if (lane == 0) wsum[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tot = 0;
+        for (unsigned i = 0; i < nwarp; ++i) {
+            unsigned long long c = wsum[i];
+            wsum[i] = tot;                 // exclusive prefix over the warps
+            tot += c;
+        }
+        base = tot ? atomicAdd(count, tot) : 0;
+    }
+    __syncthreads();
+    unsigned long long pos = base + wsum[warp];
+    for (uint64_t w = w0 + warp; w < w1; w += nwarp) {
         uint64_t v = w * 32 + lane;
         uint32_t id = v < n ? sf[v] : GC_DINF;
         bool has = id != GC_DINF;
         unsigned m = __ballot_sync(0xFFFFFFFFu, has);
-        if (!m) continue;
-        unsigned leader = __ffs(m) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xFFFFFFFFu, base, leader);
-        if (has) out[base + __popc(m & ((1u << lane) - 1))] = id;
+        if (has) out[pos + __popc(m & ((1u << lane) - 1))] = id;
+        pos += __popc(m);
     }
 }
 

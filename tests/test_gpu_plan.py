@@ -108,3 +108,30 @@ def test_profile_select_times_only_named_kernels():
     assert (host_u32(lab) == oracle.cc_uf(n, e)).all()
     g.gconn_plan_destroy(p)
     g.gconn_profile_reset()
+
+
+@pytest.mark.parametrize("spec", ["kout/remcas/naive/split_one", "hb/early/naive/none", "none/async/halve/none"])
+def test_forest_plan_replays_valid_forests(spec):
+    import torch
+    n = 25_013
+    e = graphgen.rmat(15, 70_000, 9) % np.uint32(n)
+    off, cols = graphgen.csr(n, e)
+    ref = oracle.cc_uf(n, e)
+    s, l, f, sp = spec.split("/")
+    forest = torch.empty(n, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    p = g.gconn_plan_create_forest_csr(n, dev(off), dev(cols), forest, cnt, lab,
+                                       g.make_variant(sample=s, link=l, find=f, splice=sp))
+    for _ in range(2):
+        g.gconn_plan_run(p)
+        g.gconn_sync()
+        c = int(cnt.item())
+        arcs = forest[:c].cpu().numpy().astype(np.uint64)
+        assert oracle.sf_check_arcs(n, off, cols, arcs, ref) == 0
+        assert (host_u32(lab) == ref).all()
+    g.gconn_plan_destroy(p)
+    with pytest.raises(g.GconnError) as ex:       # splice is not root-based: no forests
+        g.gconn_plan_create_forest_csr(n, dev(off), dev(cols), forest, cnt, None,
+                                       g.make_variant(sample="kout", link="remcas", splice="splice"))
+    assert ex.value.status == g.GCONN_E_UNSUPPORTED
