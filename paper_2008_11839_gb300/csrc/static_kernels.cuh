@@ -142,11 +142,13 @@ static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __re
     // Two-deep software pipeline over this warp's words: while word i's
     // unions drain, the column loads of word i+1 and the offset loads of
     // word i+2 are in flight.
-    // Words are taken from the highest vertex ids down.  Under min-linking the
-    // low ids are the hubs' roots; starting with the high-id (mostly leaf)
-    // vertices lets most first unions link a leaf under a hub by a CAS on the
-    // leaf's own entry, instead of every warp contending on the few hub roots
-    // at once (RMAT scale 22: 87 -> 78 us for this kernel).
+    // Words are taken from the highest vertex ids down.  A high-id vertex's
+    // smallest neighbour is almost always below it, so while it is still a
+    // root its first union links it by a CAS on its own entry; a low-id
+    // vertex's unions instead link its neighbours' roots under it, entries
+    // that many warps reach at once.  Starting high keeps the early, most
+    // concurrent part of the kernel on uncontended CASes (RMAT scale 22:
+    // 87 -> 78 us for this kernel).
     uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     auto load_off = [&](uint64_t ww, uint64_t& lo, uint64_t& hi) {
         uint64_t x = (nwords - 1 - ww) * 32 + lane;
