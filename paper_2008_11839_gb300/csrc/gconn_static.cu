@@ -171,6 +171,20 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off,
                               v.seed, lmax_dev, lmax_done);
         }));
         return GCONN_OK;
+    } else if (v.sample == GCONN_SAMPLE_HB && !jtb && v.hb_n <= HB_WARP_N) {
+        GC_TRY(launch_pdl("hb1", k_hb1, grid_for(k_hb1, 256, n), 256, 0, st, off, cols, n, s.P, s.sf, s.err));
+        DevBuf qbuf;
+        uint32_t qcap = n / 8 + 64;
+        GC_TRY(qbuf.alloc(sizeof(KoutJob) * (size_t)qcap, st));
+        JobQueue dq{qbuf.as<KoutJob>(), dq_count, qcap};   // count zeroed by the init kernel
+        return dispatch_uf(L, F, S, sf, [&]<int l, int f, int sp, bool w>() {
+            auto k = k_hb2w<l, f, sp, w>;
+            GC_TRY(launch_pdl("hb2", k, grid_for(k, 256, n), 256, 0, st, off, cols, v.hb_n, s, dq));
+            auto kj = k_union_jobs<l, f, sp, w>;
+            // the last block of the retry kernel also computes L_max
+            return launch_pdl("hb_deferred", kj, grid_for(kj, LMAX_SAMPLES, qcap), LMAX_SAMPLES, 0, st, s, dq,
+                              v.seed, lmax_dev, lmax_done);
+        });
     } else if (v.sample == GCONN_SAMPLE_HB) {
         GC_TRY(launch("hb1", k_hb1, grid_for(k_hb1, 256, n), 256, 0, st, off, cols, n, s.P, s.sf, s.err));
         if (jtb) {

@@ -311,6 +311,7 @@ static __global__ void __launch_bounds__(LMAX_SAMPLES) k_union_jobs(UFState s, J
 // neighbour w = cols[off[v]].  Each thread writes only its own P[v].
 static __global__ void k_hb1(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols, uint32_t n,
                       uint32_t* P, uint32_t* sf, uint32_t* err) {
+    pdl_entry();
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         uint64_t lo = off[v];
@@ -322,6 +323,66 @@ static __global__ void k_hb1(const uint64_t* __restrict__ off, const uint32_t* _
                 if (sf) sf[v] = (uint32_t)lo;
             }
         }
+    }
+}
+
+// HB sampling step 2 with the k-out machinery: a warp takes 32 consecutive
+// vertices, keeps those still roots after step 1 (no smaller first
+// neighbour, read from the row), packs the unions of their first
+// N <= HB_WARP_N arcs into a per-warp job list in shared memory (ballot
+// prefix) and drains it with all lanes; a union still climbing after
+// KOUT_FAST_STEPS steps is deferred to k_union_jobs.  A thread per vertex
+// would leave most lanes idle while a few run four unions in sequence.
+constexpr int HB_WARP_N = 4;
+
+template <int L, int F, int S, bool SF>
+static __global__ void __launch_bounds__(256) k_hb2w(const uint64_t* __restrict__ off,
+                                                     const uint32_t* __restrict__ cols, int N, UFState s,
+                                                     JobQueue dq) {
+    pdl_entry();
+    __shared__ KoutJob jobs[256 / 32][32 * HB_WARP_N];
+    KoutJob* my = jobs[threadIdx.x / 32];
+    const unsigned lane = lane_id(), lt = (1u << lane) - 1;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    const uint64_t nwords = ((uint64_t)s.n + 31) / 32;
+    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nwords; w += nwarps) {
+        uint64_t v = w * 32 + lane;
+        uint64_t lo = 0, hi = 0;
+        if (v < s.n) {
+            lo = off[v];
+            hi = off[v + 1];
+        }
+        uint32_t c[HB_WARP_N];
+        bool root = hi > lo;
+#pragma unroll
+        for (int j = 0; j < HB_WARP_N; ++j) c[j] = (j < N && hi > lo + (uint64_t)j) ? cols[lo + j] : GC_DINF;
+        if (root && c[0] < (uint32_t)v) root = false;            // hooked in step 1
+        unsigned total = 0;
+#pragma unroll
+        for (int j = 0; j < HB_WARP_N; ++j) {
+            if (c[j] != GC_DINF && c[j] >= s.n) atomicOr(s.err, GC_DERR_RANGE);
+            bool want = root && c[j] < s.n && c[j] != (uint32_t)v;
+            unsigned m = __ballot_sync(0xFFFFFFFFu, want);
+            if (want) my[total + __popc(m & lt)] = KoutJob{(uint32_t)v, c[j], (uint32_t)(lo + j)};
+            total += __popc(m);
+        }
+        __syncwarp();
+        for (unsigned j = lane; j < total; j += 32) {
+            KoutJob jb = my[j];
+            if (dq.jobs) {
+                Spin fast(KOUT_FAST_STEPS, true);
+                uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, fast);
+                if (!fast.dead) continue;
+                unsigned long long slot = atomicAdd(dq.count, 1ull);
+                if (slot < dq.cap) {
+                    dq.jobs[slot] = jb;
+                    continue;
+                }
+            }
+            Spin sp(s.cap);
+            uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
+        }
+        __syncwarp();
     }
 }
 
