@@ -148,6 +148,12 @@ struct CsrScratch {
     DevBuf lmax, counters, active, small, tasks, over;
 };
 
+// HB with a union-find (not JTB) and N <= HB_WARP_N: step 1 is fused into
+// the initialisation (k_hb_init) and step 2 runs warp-packed.
+bool hb_fused(const Variant& v, const UFState& s) {
+    return v.sample == GCONN_SAMPLE_HB && v.link != GCONN_LINK_JTB && v.hb_n <= HB_WARP_N && !s.W;
+}
+
 gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,
                         uint32_t* lmax_dev, unsigned long long* dq_count, uint32_t* lmax_done, cudaStream_t st) {
     uint32_t n = s.n;
@@ -171,8 +177,7 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off,
                               v.seed, lmax_dev, lmax_done);
         }));
         return GCONN_OK;
-    } else if (v.sample == GCONN_SAMPLE_HB && !jtb && v.hb_n <= HB_WARP_N) {
-        GC_TRY(launch_pdl("hb1", k_hb1, grid_for(k_hb1, 256, n), 256, 0, st, off, cols, n, s.P, s.sf, s.err));
+    } else if (hb_fused(v, s)) {   // step 1 already done by k_hb_init
         DevBuf qbuf;
         uint32_t qcap = n / 8 + 64;
         GC_TRY(qbuf.alloc(sizeof(KoutJob) * (size_t)qcap, st));
@@ -263,11 +268,16 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
     uint32_t* lmax = sampled ? hdr : nullptr;
     uint32_t* cnt = hdr + 1;
     unsigned long long* dq_count = reinterpret_cast<unsigned long long*>(hdr + 8);
-    GC_TRY(init_state(s, st, hdr, 16));
     // the rounds-based finishes (SV, LT) sample with Union-Async
     Variant sv = v;
     bool rounds = is_rounds_link(v.link);
     if (rounds) { sv.link = GCONN_LINK_ASYNC; sv.find = GCONN_FIND_NAIVE; sv.splice = 0; }
+    if (hb_fused(sv, s)) {   // InitLabel and HB step 1 in one pass
+        GC_TRY(launch_pdl("init", k_hb_init, grid_for(k_hb_init, 256, n), 256, 0, st, off, cols, n, s.P, s.H, s.sf,
+                          s.err, hdr, 16u));
+    } else {
+        GC_TRY(init_state(s, st, hdr, 16));
+    }
     if (sampled) GC_TRY(csr_sample(sv, s, off, cols, lmax, dq_count, hdr + 10, st));
     // vertex gathering
     uint64_t task_cap = (uint64_t)n + 1024;

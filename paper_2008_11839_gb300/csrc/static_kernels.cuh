@@ -326,6 +326,35 @@ static __global__ void k_hb1(const uint64_t* __restrict__ off, const uint32_t* _
     }
 }
 
+// InitLabel fused with HB step 1 (Algorithm 3): P[v] = the smallest
+// neighbour w = cols[off[v]] when w < v, else v; a hooked vertex's forest slot
+// records arc off[v]; hooks are cleared and so is `zero` (the pass's
+// counters).  Every thread writes only its own entries and nothing reads P in
+// this kernel, so step 1 needs no separate initialisation pass before it.
+static __global__ void k_hb_init(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols, uint32_t n,
+                                 uint32_t* P, uint32_t* H, uint32_t* sf, uint32_t* err, uint32_t* zero,
+                                 uint32_t nzero) {
+    pdl_entry();
+    if (zero && blockIdx.x == 0)
+        for (uint32_t i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint64_t lo = off[v];
+        uint32_t p = (uint32_t)v, e = GC_DINF;
+        if (off[v + 1] > lo) {
+            uint32_t w = cols[lo];
+            if (w >= n) atomicOr(err, GC_DERR_RANGE);
+            else if (w < (uint32_t)v) {
+                p = w;
+                e = (uint32_t)lo;
+            }
+        }
+        P[v] = p;
+        if (H) H[v] = GC_DINF;
+        if (sf) sf[v] = e;
+    }
+}
+
 // HB sampling step 2 with the k-out machinery: a warp takes 32 consecutive
 // vertices, keeps those still roots after step 1 (no smaller first
 // neighbour, read from the row), packs the unions of their first
@@ -345,25 +374,40 @@ static __global__ void __launch_bounds__(256) k_hb2w(const uint64_t* __restrict_
     const unsigned lane = lane_id(), lt = (1u << lane) - 1;
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
     const uint64_t nwords = ((uint64_t)s.n + 31) / 32;
-    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < nwords; w += nwarps) {
-        uint64_t v = w * 32 + lane;
-        uint64_t lo = 0, hi = 0;
-        if (v < s.n) {
-            lo = off[v];
-            hi = off[v + 1];
+    // as in k_kout: words from the highest ids down, offsets of word i+2 and
+    // columns of word i+1 in flight while word i's unions drain
+    auto load_off = [&](uint64_t ww, uint64_t& lo, uint64_t& hi) {
+        uint64_t x = (nwords - 1 - ww) * 32 + lane;
+        lo = hi = 0;
+        if (ww < nwords && x < s.n) {
+            lo = off[x];
+            hi = off[x + 1];
         }
-        uint32_t c[HB_WARP_N];
-        bool root = hi > lo;
+    };
+    auto load_cols = [&](uint64_t lo, uint64_t hi, uint32_t* c) {
 #pragma unroll
         for (int j = 0; j < HB_WARP_N; ++j) c[j] = (j < N && hi > lo + (uint64_t)j) ? cols[lo + j] : GC_DINF;
-        if (root && c[0] < (uint32_t)v) root = false;            // hooked in step 1
+    };
+    uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    uint64_t lo0, hi0, lo1, hi1;
+    uint32_t c[HB_WARP_N];
+    load_off(w, lo0, hi0);
+    load_off(w + nwarps, lo1, hi1);
+    load_cols(lo0, hi0, c);
+    for (; w < nwords; w += nwarps) {
+        uint32_t cn[HB_WARP_N];
+        uint64_t lo2, hi2;
+        load_cols(lo1, hi1, cn);
+        load_off(w + 2 * nwarps, lo2, hi2);
+        uint64_t v = (nwords - 1 - w) * 32 + lane;
+        bool root = hi0 > lo0 && !(c[0] < (uint32_t)v);   // not hooked in step 1
         unsigned total = 0;
 #pragma unroll
         for (int j = 0; j < HB_WARP_N; ++j) {
             if (c[j] != GC_DINF && c[j] >= s.n) atomicOr(s.err, GC_DERR_RANGE);
             bool want = root && c[j] < s.n && c[j] != (uint32_t)v;
             unsigned m = __ballot_sync(0xFFFFFFFFu, want);
-            if (want) my[total + __popc(m & lt)] = KoutJob{(uint32_t)v, c[j], (uint32_t)(lo + j)};
+            if (want) my[total + __popc(m & lt)] = KoutJob{(uint32_t)v, c[j], (uint32_t)(lo0 + j)};
             total += __popc(m);
         }
         __syncwarp();
@@ -383,6 +427,10 @@ static __global__ void __launch_bounds__(256) k_hb2w(const uint64_t* __restrict_
             uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
         }
         __syncwarp();
+        lo0 = lo1; hi0 = hi1;
+#pragma unroll
+        for (int j = 0; j < HB_WARP_N; ++j) c[j] = cn[j];
+        lo1 = lo2; hi1 = hi2;
     }
 }
 
