@@ -145,7 +145,7 @@ gconn_status sf_output(uint32_t n, const uint32_t* sf, uint64_t* forest, uint64_
 
 // ---------------------------------------------------------------- CSR path
 struct CsrScratch {
-    DevBuf lmax, counters, active, small, tasks, over;
+    DevBuf counters, active, small, tasks, over;
 };
 
 // HB with a union-find (not JTB) and N <= HB_WARP_N: step 1 is fused into
