@@ -836,6 +836,54 @@ def run_sweep(args):
     print(json.dumps({"sweep_best": ok[:10], "all_exact": all(r["exact"] for r in ok), "variants": len(rows)}))
 
 
+def run_ablation(args):
+    """The contribution of the GB300 forms of the paper's GPU optimisations
+    (Section 3.3: coalesced / reorganised sampling reads, vertex gathering) on
+    the RMAT s22 CSR: the default pass against its plain forms, each as a
+    captured plan, labels checked against the oracle."""
+    import torch
+    import oracle
+    import paper_2008_11839_gb300 as g
+    g.build()
+    dev = torch.device("cuda", 0)
+    n, e, off, cols, seed = make_static_input(0, args.scale, args.edges)
+    ref = oracle.cc_uf(n, e)
+    d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+    d_cols = torch.from_numpy(cols.view(np.int32)).to(dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    forms = [(0, "library kernels"), (1, "plain k-out (thread per vertex)"),
+             (2, "no vertex gathering (thread-per-vertex finish)"), (3, "both plain")]
+    rows = []
+    for spec in args.ablation_variants.split(","):
+        for bits, what in forms:
+            v = parse_variant(g, spec)
+            v.ablation = bits
+            plan = g.gconn_plan_create_cc_csr(n, d_off, d_cols, labels, v)
+            for i in range(3):
+                flush.fill_(i)
+                g.gconn_plan_run(plan, stream)
+            g.gconn_sync(stream)
+            exact = bool((labels.cpu().numpy().view(np.uint32) == ref).all())
+            ts = []
+            for i in range(args.steps):
+                flush.fill_(i + 300)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                g.gconn_plan_run(plan, stream)
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            g.gconn_sync(stream)
+            g.gconn_plan_destroy(plan)
+            ms = float(np.median(ts))
+            row = {"variant": spec, "ablation": bits, "form": what, "ms": round(ms, 4),
+                   "edges_per_s": args.edges / (ms * 1e-3), "exact": exact}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+
+
 def run_stats(args):
     """Sampling quality on the RMAT s22 graph (the paper's Table 4 columns):
     Cov, IC, Time % and arcs inspected, per sampling method."""
@@ -922,6 +970,9 @@ def main():
     ap.add_argument("--scale", type=int, default=SCALE, help="RMAT scale (default: the scale-22 workload)")
     ap.add_argument("--edges", type=int, default=M_EDGES, help="undirected edges (default 2^26)")
     ap.add_argument("--sweep", action="store_true", help="time every sampling x finish variant (RMAT s22)")
+    ap.add_argument("--ablation", action="store_true", help="library kernels vs their plain forms (RMAT s22)")
+    ap.add_argument("--ablation-variants", default="kout/remcas/naive/split_one,kout/early/naive/none,"
+                                                   "hb/remcas/naive/split_one")
     ap.add_argument("--sweep-samples", default="none,kout,hb,bfs")
     ap.add_argument("--sweep-steps", type=int, default=5)
     ap.add_argument("--stats", action="store_true", help="sampling Cov / IC / Time %% per sampling method")
@@ -937,6 +988,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.sweep:
         run_sweep(args)
+        return
+    if args.ablation:
+        run_ablation(args)
         return
     if args.stats:
         run_stats(args)

@@ -102,8 +102,19 @@ typedef struct gconn_variant {
     int32_t block;      /* threads per block, 0 = library default */
     uint64_t seed;      /* L_max / BFS-source sampling and Union-JTB priorities */
     uint32_t iter_cap;  /* per-operation loop cap, 0 = default (2^24) */
-    uint32_t reserved;  /* must be 0 */
+    uint32_t ablation;  /* 0 = the library's kernels; GCONN_ABL_* bits select plain forms
+                           for measurement (results are the same) */
 } gconn_variant;
+
+/* Ablation bits (measurement only, CSR input; no paper counterpart beyond the
+ * optimisations they switch off, Section 3.3):
+ *   GCONN_ABL_PLAIN_SAMPLE: k-out sampling with one thread per vertex walking
+ *     its first k arcs (no per-warp packing of unions, no deferral);
+ *   GCONN_ABL_NO_VG: no vertex gathering -- full compression, then a finish
+ *     with one thread per vertex over its whole row, skipping vertices whose
+ *     parent is L_max (no active lists, no load balancing). */
+#define GCONN_ABL_PLAIN_SAMPLE 1u
+#define GCONN_ABL_NO_VG 2u
 
 /* Fill *v with the library default (Union-Async, naive find, k-out k=2 for
  * CSR input and no sampling for COO input).  Returns GCONN_E_INVAL on NULL. */

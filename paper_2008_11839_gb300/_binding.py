@@ -62,7 +62,7 @@ class gconn_variant(ctypes.Structure):
     _fields_ = [("sample", ctypes.c_int32), ("k", ctypes.c_int32), ("hb_n", ctypes.c_int32),
                 ("link", ctypes.c_int32), ("find", ctypes.c_int32), ("splice", ctypes.c_int32),
                 ("lt_rules", ctypes.c_int32), ("block", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("iter_cap", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("iter_cap", ctypes.c_uint32), ("ablation", ctypes.c_uint32)]
 
 
 GCONN_BATCH_CLASSES = 4
@@ -80,6 +80,7 @@ class gconn_batch_tune(ctypes.Structure):
 
 
 GCONN_OP_INSERT, GCONN_OP_QUERY = 0, 1
+GCONN_ABL_PLAIN_SAMPLE, GCONN_ABL_NO_VG = 1, 2
 
 
 class gconn_server_config(ctypes.Structure):
@@ -233,7 +234,7 @@ def check(status: int, what: str = "") -> None:
 
 
 def make_variant(sample="none", link="async", find="naive", splice="none", lt="PRF", k=2, hb_n=4,
-                 block=0, seed=0x6C0A0001, iter_cap=0) -> gconn_variant:
+                 block=0, seed=0x6C0A0001, iter_cap=0, ablation=0) -> gconn_variant:
     v = gconn_variant()
     check(lib().gconn_variant_default(ctypes.byref(v)), "gconn_variant_default")
     v.sample = SAMPLES[sample] if isinstance(sample, str) else int(sample)
@@ -241,7 +242,7 @@ def make_variant(sample="none", link="async", find="naive", splice="none", lt="P
     v.find = FINDS[find] if isinstance(find, str) else int(find)
     v.splice = SPLICES[splice] if isinstance(splice, str) else int(splice)
     v.lt_rules = lt_rules(lt) if isinstance(lt, str) else int(lt)
-    v.k, v.hb_n, v.block, v.seed, v.iter_cap = k, hb_n, block, seed, iter_cap
+    v.k, v.hb_n, v.block, v.seed, v.iter_cap, v.ablation = k, hb_n, block, seed, iter_cap, ablation
     return v
 
 

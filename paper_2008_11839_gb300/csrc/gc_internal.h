@@ -139,6 +139,7 @@ struct Variant {
     int sample, k, hb_n, link, find, splice, lt_rules, block;
     uint64_t seed;
     uint32_t cap;
+    int ablation;   // GCONN_ABL_* bits
 };
 gconn_status resolve_variant(const gconn_variant* in, int input_kind, int want_forest, Variant* out);
 

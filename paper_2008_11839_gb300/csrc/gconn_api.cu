@@ -324,6 +324,7 @@ gconn_status resolve_variant(const gconn_variant* in, int input_kind, int want_f
     out->lt_rules = d.lt_rules;
     out->block = d.block;
     out->seed = d.seed;
+    out->ablation = (int)d.ablation;
     out->cap = d.iter_cap ? d.iter_cap : DEFAULT_CAP;
     return GCONN_OK;
 }
@@ -376,7 +377,7 @@ extern "C" gconn_status gconn_variant_check(const gconn_variant* v, int input_ki
     if (!v) return GCONN_E_INVAL;
     if (input_kind != 0 && input_kind != 1) return GCONN_E_INVAL;
     if (want_forest < 0 || want_forest > 2) return GCONN_E_INVAL;
-    if (v->reserved != 0) return GCONN_E_INVAL;
+    if (v->ablation & ~(GCONN_ABL_PLAIN_SAMPLE | GCONN_ABL_NO_VG)) return GCONN_E_INVAL;
     if (v->sample < 0 || v->sample > GCONN_SAMPLE_BFS) return GCONN_E_INVAL;
     if (v->link < 0 || v->link > GCONN_LINK_STERGIOU) return GCONN_E_INVAL;
     if (v->find < 0 || v->find > GCONN_FIND_FULLSHORTCUT) return GCONN_E_INVAL;

@@ -158,7 +158,7 @@ extern "C" gconn_status gconn_cc_csr_noalloc(uint32_t n, const uint64_t* offsets
         if (v.sample == GCONN_SAMPLE_KOUT) {
             auto k = k_kout<l, fr, sp, false>;
             GC_TRY(launch("kout", k, grid_for(k, KOUT_BLOCK, n), KOUT_BLOCK, 0, st, offsets, cols, v.k, s,
-                          JobQueue{nullptr, nullptr, 0}));
+                          JobQueue{nullptr, nullptr, 0}, false));
         } else if (v.sample == GCONN_SAMPLE_HB) {
             GC_TRY(launch("hb1", k_hb1, grid_for(k_hb1, 256, n), 256, 0, st, offsets, cols, n, s.P, s.sf, s.err));
             auto k = k_hb2<l, fr, sp, false>;

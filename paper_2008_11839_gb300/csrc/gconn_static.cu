@@ -170,7 +170,8 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const uint64_t* off,
         JobQueue dq{qbuf.as<KoutJob>(), dq_count, qcap};   // count zeroed by the init kernel
         GC_TRY(dispatch_uf(L, F, S, sf, [&]<int l, int f, int sp, bool w>() {
             auto k = k_kout<l, f, sp, w>;
-            GC_TRY(launch_pdl("kout", k, grid_for(k, KOUT_BLOCK, n), KOUT_BLOCK, 0, st, off, cols, v.k, s, dq));
+            GC_TRY(launch_pdl("kout", k, grid_for(k, KOUT_BLOCK, n), KOUT_BLOCK, 0, st, off, cols, v.k, s, dq,
+                              (v.ablation & GCONN_ABL_PLAIN_SAMPLE) != 0));
             auto kj = k_union_jobs<l, f, sp, w>;
             // the last block of the retry kernel also computes L_max
             return launch_pdl("kout_deferred", kj, grid_for(kj, LMAX_SAMPLES, qcap), LMAX_SAMPLES, 0, st, s, dq,
@@ -279,6 +280,17 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
         GC_TRY(init_state(s, st, hdr, 16));
     }
     if (sampled) GC_TRY(csr_sample(sv, s, off, cols, lmax, dq_count, hdr + 10, st));
+    if (v.ablation & GCONN_ABL_NO_VG) {   // measurement form: full compression, then the plain finish
+        if (rounds || sv.link == GCONN_LINK_JTB || stats) return GCONN_E_UNSUPPORTED;
+        GC_TRY(compress_all(sv, s, st));
+        int L, F, S;
+        uf_triple(v, &L, &F, &S);
+        int B = block_of(v);
+        return dispatch_uf(L, F, S, s.sf != nullptr, [&]<int l, int f, int sp, bool w>() {
+            auto k = k_finish_plain<l, f, sp, w>;
+            return launch_pdl("finish", k, grid_for(k, B, n), B, 0, st, off, cols, s, (const uint32_t*)lmax);
+        });
+    }
     // vertex gathering
     uint64_t task_cap = (uint64_t)n + 1024;
     uint32_t* active = nullptr;

@@ -114,12 +114,14 @@ struct JobQueue {
 };
 
 template <int L, int F, int S, bool SF>
+// plain: one thread per vertex over its first k arcs (the form without the
+// per-warp packing; also taken for k > KOUT_WARP_K).
 static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __restrict__ off,
                                                             const uint32_t* __restrict__ cols, int k, UFState s,
-                                                            JobQueue dq) {
+                                                            JobQueue dq, bool plain) {
     pdl_entry();
     __shared__ KoutJob jobs[KOUT_BLOCK / 32][32 * KOUT_WARP_K];
-    if (k > KOUT_WARP_K) {
+    if (k > KOUT_WARP_K || plain) {
         uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
         for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
             uint64_t lo = off[v], hi = off[v + 1];
@@ -803,6 +805,32 @@ __global__ void __launch_bounds__(256) k_finish(const uint64_t* __restrict__ off
             if (!arc_needed(active, u, v)) continue;
             Spin sp(s.cap);
             uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
+        }
+    }
+}
+
+// Finish without vertex gathering (measurement form, GCONN_ABL_NO_VG): one
+// thread per vertex; a vertex whose parent is L_max (after the full
+// compression) is skipped, any other unions its whole row in sequence.  Each
+// undirected edge between two processed vertices is unioned from both sides.
+// Skipping stays exact: a vertex seen with parent L_max is in L_max's tree,
+// membership never ends, so an edge skipped from both ends joins two vertices
+// already connected.
+template <int L, int F, int S, bool SF>
+static __global__ void __launch_bounds__(256) k_finish_plain(const uint64_t* __restrict__ off,
+                                                             const uint32_t* __restrict__ cols, UFState s,
+                                                             const uint32_t* lmax_p) {
+    pdl_entry();
+    uint32_t lmax = lmax_p ? *lmax_p : GC_DINF;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
+        if (ldp(s.P, (uint32_t)v) == lmax) continue;
+        for (uint64_t a = off[v]; a < off[v + 1]; ++a) {
+            uint32_t u = cols[a];
+            if (u >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
+            if (u == (uint32_t)v) continue;
+            Spin sp(s.cap);
+            uf_union<L, F, S, SF>(s, (uint32_t)v, u, (uint32_t)a, sp);
         }
     }
 }

@@ -65,8 +65,10 @@ def test_forest_needs_root_based_lt(lib):
 
 def test_out_of_range_fields(lib):
     v = g.make_variant()
-    v.reserved = 1
+    v.ablation = 4                            # only the two documented ablation bits exist
     assert g.gconn_variant_check(v, 0, 0) == b.GCONN_E_INVAL
+    v.ablation = b.GCONN_ABL_PLAIN_SAMPLE | b.GCONN_ABL_NO_VG
+    assert g.gconn_variant_check(v, 1, 0) == 0
     v = g.make_variant(block=100)
     assert g.gconn_variant_check(v, 0, 0) == b.GCONN_E_INVAL
     v = g.make_variant()

@@ -185,6 +185,25 @@ def test_large_host_csr_inputs(shape):
         assert (lab == ref).all(), spec
 
 
+@pytest.mark.parametrize("ablation", [1, 2, 3])
+@pytest.mark.parametrize("spec", ["kout/remcas/naive/split_one", "kout/early/naive/none", "hb/async/halve/none",
+                                  "none/remcas/naive/splice"])
+def test_ablation_forms_exact(ablation, spec):
+    """The measurement forms (plain k-out, finish without vertex gathering)
+    reach the same canonical labels, and valid forests."""
+    s, l, f, sp = spec.split("/")
+    for name, n, e in GRAPHS[:4]:
+        off, cols = CSR[name]
+        v = g.make_variant(sample=s, link=l, find=f, splice=sp, ablation=ablation)
+        lab = g.cc_csr(n, dev(off), dev(cols), v)
+        g.gconn_sync()
+        assert (host_u32(lab) == REF[name]).all(), (name, spec, ablation)
+        if sp != "splice":
+            ids, _ = g.spanning_forest_csr(n, dev(off), dev(cols), v)
+            g.gconn_sync()
+            assert oracle.sf_check_arcs(n, off, cols, ids.cpu().numpy().astype(np.uint64), REF[name]) == 0
+
+
 def test_release_cached_then_rerun():
     """Scratch memory is cached between calls; releasing it leaves later calls exact."""
     import torch
