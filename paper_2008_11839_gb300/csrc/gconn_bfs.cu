@@ -92,14 +92,51 @@ __global__ void __launch_bounds__(256) k_bfs_td(const uint64_t* __restrict__ off
     }
 }
 
+// Block-wide append (blocks of BFS_BU_BLOCK threads, every thread calling):
+// one reservation on the shared queue counters per block instead of one per
+// warp -- a bottom-up level can discover millions of vertices, and per-warp
+// atomics on the same two counters serialise at their L2 slice.
+constexpr int BFS_BU_BLOCK = 256;
+
+__device__ __forceinline__ void block_append(bool has, uint32_t val, uint64_t deg, uint32_t* q, BfsCounters* c) {
+    __shared__ uint32_t wcnt[BFS_BU_BLOCK / 32];
+    __shared__ unsigned long long wdeg[BFS_BU_BLOCK / 32];
+    __shared__ uint32_t bbase;
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x / 32;
+    unsigned m = __ballot_sync(0xFFFFFFFFu, has);
+    unsigned long long dsum = has ? deg : 0;
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xFFFFFFFFu, dsum, o);
+    if (lane == 0) {
+        wcnt[warp] = __popc(m);
+        wdeg[warp] = dsum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        unsigned long long dtot = 0;
+        for (int i = 0; i < BFS_BU_BLOCK / 32; ++i) {
+            uint32_t x = wcnt[i];
+            wcnt[i] = tot;                 // exclusive prefix over the warps
+            tot += x;
+            dtot += wdeg[i];
+        }
+        bbase = tot ? atomicAdd(&c->qlen, tot) : 0;
+        if (dtot) atomicAdd(&c->degsum, dtot);
+    }
+    __syncthreads();
+    if (has) q[bbase + wcnt[warp] + __popc(m & ((1u << lane) - 1))] = val;
+    __syncthreads();                       // wcnt / bbase are reused by the next round
+}
+
 // Bottom-up step: every unvisited vertex looks for a parent in the frontier.
-__global__ void __launch_bounds__(256) k_bfs_bu(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols,
-                                                uint32_t n, uint32_t level, uint32_t* dist, uint32_t* next,
-                                                BfsCounters* c, uint32_t* sf, uint32_t* err) {
+__global__ void __launch_bounds__(BFS_BU_BLOCK) k_bfs_bu(const uint64_t* __restrict__ off,
+                                                         const uint32_t* __restrict__ cols, uint32_t n,
+                                                         uint32_t level, uint32_t* dist, uint32_t* next,
+                                                         BfsCounters* c, uint32_t* sf, uint32_t* err) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint64_t start = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t rounds = ((uint64_t)n + stride - 1) / stride;
-    for (uint64_t r = 0; r < rounds; ++r) {     // uniform trip count for the warp vote
+    for (uint64_t r = 0; r < rounds; ++r) {     // uniform trip count for the block-wide append
         uint64_t v = start + r * stride;
         bool found = false;
         uint64_t deg = 0;
@@ -117,7 +154,7 @@ __global__ void __launch_bounds__(256) k_bfs_bu(const uint64_t* __restrict__ off
                 }
             }
         }
-        warp_append(found, (uint32_t)v, deg, next, c);
+        block_append(found, (uint32_t)v, deg, next, c);
     }
 }
 
@@ -157,9 +194,17 @@ gconn_status bfs_sample(const Variant& v, const UFState& s, const uint64_t* off,
     uint32_t* qa = q0.as<uint32_t>();
     uint32_t* qb = q1.as<uint32_t>();
     BfsCounters* c = cbuf.as<BfsCounters>();
-    BfsCounters* hc = nullptr;
-    GC_CUDA(cudaMallocHost(&hc, sizeof(BfsCounters)));
-    struct HostFree { BfsCounters* p; ~HostFree() { cudaFreeHost(p); } } hf{hc};
+    // The per-level counter read-back goes through a pinned buffer kept per
+    // host thread (a pinned allocation per call would cost more than a level).
+    struct PinnedCounters {
+        BfsCounters* p = nullptr;
+        ~PinnedCounters() {
+            if (p) cudaFreeHost(p);
+        }
+    };
+    static thread_local PinnedCounters pinned;
+    if (!pinned.p) GC_CUDA(cudaMallocHost(&pinned.p, sizeof(BfsCounters)));
+    BfsCounters* hc = pinned.p;
 
     uint64_t narcs = 0;
     GC_CUDA(cudaMemcpyAsync(&narcs, off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
