@@ -190,8 +190,9 @@ static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __re
                 uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, fast);
                 if (!fast.dead) continue;
                 unsigned long long slot = atomicAdd(dq.count, 1ull);
-                if (slot < dq.cap) {
-                    dq.jobs[slot] = jb;
+                if (slot < dq.cap) {   // resume where the climb stopped (see Spin)
+                    dq.jobs[slot] = KoutJob{fast.at_u != GC_DINF ? fast.at_u : jb.u,
+                                            fast.at_v != GC_DINF ? fast.at_v : jb.v, jb.eid};
                     continue;
                 }
             }
@@ -420,8 +421,9 @@ static __global__ void __launch_bounds__(256) k_hb2w(const uint64_t* __restrict_
                 uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, fast);
                 if (!fast.dead) continue;
                 unsigned long long slot = atomicAdd(dq.count, 1ull);
-                if (slot < dq.cap) {
-                    dq.jobs[slot] = jb;
+                if (slot < dq.cap) {   // resume where the climb stopped (see Spin)
+                    dq.jobs[slot] = KoutJob{fast.at_u != GC_DINF ? fast.at_u : jb.u,
+                                            fast.at_v != GC_DINF ? fast.at_v : jb.v, jb.eid};
                     continue;
                 }
             }

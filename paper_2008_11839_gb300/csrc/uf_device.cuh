@@ -61,7 +61,13 @@ struct Spin {
     uint32_t left;
     bool dead;
     bool soft;   // a soft budget gives up quietly (the caller defers the operation)
-    __device__ __forceinline__ explicit Spin(uint32_t cap, bool soft_ = false) : left(cap), dead(false), soft(soft_) {}
+    // Where an abandoned union must resume (GC_DINF: from its endpoints).  A
+    // Rem climb records its current pair: SpliceAtomic may already have moved
+    // a non-root subtree into the other tree, so the two endpoints can look
+    // joined while the rest of the first set is not yet linked.
+    uint32_t at_u, at_v;
+    __device__ __forceinline__ explicit Spin(uint32_t cap, bool soft_ = false)
+        : left(cap), dead(false), soft(soft_), at_u(GC_DINF), at_v(GC_DINF) {}
     // One loop step; false once the operation must give up.
     __device__ __forceinline__ bool step(const UFState& s) {
         if (dead) return false;
@@ -252,7 +258,11 @@ __device__ __forceinline__ bool union_remcas(const UFState& s, uint32_t u, uint3
                 pu = ldq<true>(P, w);
             }
         }
-        if (!sp.step(s)) return false;
+        if (!sp.step(s)) {
+            sp.at_u = ru;
+            sp.at_v = rv;
+            return false;
+        }
     }
 }
 
@@ -311,7 +321,11 @@ __device__ __forceinline__ bool union_remlock(const UFState& s, uint32_t u, uint
                 pu = ldq<true>(P, w);
             }
         }
-        if (!sp.step(s)) return false;
+        if (!sp.step(s)) {
+            sp.at_u = ru;
+            sp.at_v = rv;
+            return false;
+        }
     }
 }
 

@@ -90,3 +90,26 @@ def test_lmax_between_equal_components_follows_the_samples(seed):
     lab0 = oracle.cc_uf(n, _sampled_edges(n, off, cols, "kout"))
     assert st.as_dict()["lmax"] == _expected_lmax(n, lab0, seed)
     assert (host_u32(lab) == oracle.cc_uf(n, e)).all()
+
+
+@pytest.mark.parametrize("link", ["remcas", "remlock"])
+def test_deferred_splice_unions_keep_the_sampled_partition(link):
+    """A k-out union that exceeds its step budget is finished later by the
+    retry kernel.  With SpliceAtomic the abandoned climb may already have moved
+    a subtree into the other tree, so it must resume from its current pair,
+    not its endpoints; otherwise (rarely) part of a set is left behind and the
+    sampled partition has an extra component.  Many repetitions make a
+    resumption bug show."""
+    import torch
+    n = 6000
+    e = graphgen.rmat(13, 30_000, 17) % np.uint32(n)
+    off, cols = graphgen.csr(n, e)
+    want = len(np.unique(oracle.cc_uf(n, _sampled_edges(n, off, cols, "kout"))))
+    ref = oracle.cc_uf(n, e)
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    d_off, d_cols = dev(off), dev(cols)
+    v = g.make_variant(sample="kout", link=link, splice="splice")
+    for _ in range(600):
+        st = g.gconn_cc_csr_stats(n, d_off, d_cols, lab, v)
+        assert st.as_dict()["sampled_components"] == want
+    assert (host_u32(lab) == ref).all()
