@@ -265,8 +265,8 @@ __global__ void k_gather_tasks(const uint64_t* off, const uint32_t* cols, uint32
 
 __global__ void k_gather_over(const uint64_t* off, const uint32_t* cols, uint32_t n, const uint32_t* active,
                               const uint32_t* over, const uint32_t* nover, Gather g, uint32_t* err) {
-    uint32_t cnt = *nover;
-    for (uint32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    uint64_t cnt = *nover;
+    for (uint64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
         uint32_t u = over[i];
         for (uint64_t a = off[u] + threadIdx.x; a < off[u + 1]; a += blockDim.x) {
             uint32_t v = cols[a];

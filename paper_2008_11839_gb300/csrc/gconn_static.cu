@@ -292,7 +292,9 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const uint64_t* off
         });
     }
     // vertex gathering
-    uint64_t task_cap = (uint64_t)n + 1024;
+    // task ids and the task counter are uint32 on the device: clamp (overflowing
+    // vertices go to the per-block overflow list)
+    uint64_t task_cap = std::min<uint64_t>((uint64_t)n + 1024, 0xFFFFFFFFull);
     uint32_t* active = nullptr;
     if (sampled) {
         GC_TRY(sc.active.alloc(sizeof(uint32_t) * (((size_t)n + 31) / 32), st));

@@ -843,8 +843,8 @@ static __global__ void __launch_bounds__(256) k_finish_over(const uint64_t* __re
                                                      const uint32_t* __restrict__ cols, UFState s,
                                                      const uint32_t* active, const uint32_t* over,
                                                      const uint32_t* nover) {
-    uint32_t cnt = *nover;
-    for (uint32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    uint64_t cnt = *nover;
+    for (uint64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
         uint32_t u = over[i];
         for (uint64_t a = off[u] + threadIdx.x; a < off[u + 1]; a += blockDim.x) {
             uint32_t v = cols[a];
