@@ -42,6 +42,9 @@ __global__ void __launch_bounds__(256) k_query(const uint2* __restrict__ Q, uint
         if (L == LK_JTB) {
             a = jtb_find<F>(s, e.x, sp);
             b = jtb_find<F>(s, e.y, sp);
+        } else if (F == FD_NAIVE) {
+            out[i] = same_root_lockstep(s, e.x, e.y, sp) ? 1 : 0;
+            continue;
         } else {
             a = uf_find<F, true>(s, e.x, sp);   // no link happens during a query batch
             b = uf_find<F, true>(s, e.y, sp);

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(256) k_serve(const uint2* __restrict__ pairs, 
             uint8_t a = 0;
             if (inrange) {
                 if (L == LK_JTB) a = jtb_find<F>(s, e.x, sp) == jtb_find<F>(s, e.y, sp);
+                else if (F == FD_NAIVE) a = same_root_lockstep(s, e.x, e.y, sp);
                 else a = uf_find<F, true>(s, e.x, sp) == uf_find<F, true>(s, e.y, sp);
             }
             out[g.out + (i - g.start)] = a;

@@ -468,6 +468,24 @@ __device__ __forceinline__ bool same_set(const UFState& s, uint32_t x, uint32_t 
     return false;
 }
 
+// Both endpoints' walks in lock step, for queries under the naive find while
+// nothing links or compresses the forest (query batches, query segments).
+// Every rule but JTB keeps P[v] <= v, so each tree's root is its smallest
+// vertex: a walk that reaches a root above the other walk's current vertex
+// proves the two sets differ without walking the other path to its end.  One
+// dependent load per step pair instead of the two walks one after the other.
+__device__ __forceinline__ bool same_root_lockstep(const UFState& s, uint32_t x, uint32_t y, Spin& sp) {
+    while (x != y) {
+        uint32_t px = ldq<true>(s.P, x), py = ldq<true>(s.P, y);
+        bool rx = px == x, ry = py == y;
+        if ((rx && (ry || y < x)) || (ry && x < y)) return false;
+        x = px;
+        y = py;
+        if (!sp.step(s)) return false;
+    }
+    return true;
+}
+
 // ----------------------------------------------------------- dispatcher
 template <int L, int F, int S, bool SF>
 __device__ __forceinline__ bool uf_union(const UFState& s, uint32_t u, uint32_t v, uint32_t eid, Spin& sp) {
