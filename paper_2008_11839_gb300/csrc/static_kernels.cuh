@@ -90,10 +90,15 @@ static __global__ void __launch_bounds__(256) k_union_coo(const uint2* __restric
 
 // k-out sampling (Algorithm 2, first k edges of every vertex).  A warp takes
 // 32 consecutive vertices, reads their first k <= KOUT_WARP_K column entries
-// (one sector per row), and packs the union jobs into a per-warp list in
-// shared memory with a ballot prefix, so all 32 lanes then drain a dense list:
-// isolated vertices (often ~40 % of an RMAT graph) and short rows leave no lane
-// idle.  Larger k falls back to one thread per vertex.
+// (one sector per row), and packs one job per vertex with a sampled arc into
+// a per-warp list in shared memory with a ballot prefix: isolated vertices
+// (often ~40 % of an RMAT graph) leave the high lanes idle instead of
+// scattering idle lanes through the warp.  A lane runs its vertex's unions one
+// after the other (RMAT scale 22: 79 -> 73 us against one job per arc, where
+// a vertex's two unions raced for its own entry on two lanes; refilling the
+// idle lanes from the next word, 32 jobs per round, took 83-85 us: more
+// unions at once only add contention).  Larger k falls back to one thread per
+// vertex.
 constexpr int KOUT_WARP_K = 2;
 constexpr int KOUT_BLOCK = 256;
 
@@ -113,6 +118,25 @@ struct JobQueue {
     uint32_t cap;
 };
 
+// One union under the soft budget when a queue is given: an abandoned union
+// goes to the queue (or, if it is full, runs on with the full cap).
+template <int L, int F, int S, bool SF>
+__device__ __forceinline__ void union_or_defer(const UFState& s, const JobQueue& dq, uint32_t a, uint32_t b,
+                                               uint32_t eid) {
+    if (dq.jobs) {
+        Spin fast(KOUT_FAST_STEPS, true);
+        uf_union<L, F, S, SF>(s, a, b, eid, fast);
+        if (!fast.dead) return;
+        unsigned long long slot = atomicAdd(dq.count, 1ull);
+        if (slot < dq.cap) {   // resume where the climb stopped (see Spin)
+            dq.jobs[slot] = KoutJob{fast.at_u != GC_DINF ? fast.at_u : a, fast.at_v != GC_DINF ? fast.at_v : b, eid};
+            return;
+        }
+    }
+    Spin sp(s.cap);
+    uf_union<L, F, S, SF>(s, a, b, eid, sp);
+}
+
 template <int L, int F, int S, bool SF>
 // plain: one thread per vertex over its first k arcs (the form without the
 // per-warp packing; also taken for k > KOUT_WARP_K).
@@ -120,7 +144,7 @@ static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __re
                                                             const uint32_t* __restrict__ cols, int k, UFState s,
                                                             JobQueue dq, bool plain) {
     pdl_entry();
-    __shared__ KoutJob jobs[KOUT_BLOCK / 32][32 * KOUT_WARP_K];
+    __shared__ uint4 jobs[KOUT_BLOCK / 32][32];   // (v, first arc, second arc, arc index)
     if (k > KOUT_WARP_K || plain) {
         uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
         for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
@@ -136,7 +160,7 @@ static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __re
         }
         return;
     }
-    KoutJob* my = jobs[threadIdx.x / 32];
+    uint4* my = jobs[threadIdx.x / 32];
     unsigned lane = lane_id();
     unsigned lt = (1u << lane) - 1;
     uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
@@ -178,26 +202,17 @@ static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __re
         if ((c0 != GC_DINF && c0 >= s.n) || (c1 != GC_DINF && c1 >= s.n)) atomicOr(s.err, GC_DERR_RANGE);
         bool j0 = c0 < s.n && c0 != (uint32_t)v;
         bool j1 = c1 < s.n && c1 != (uint32_t)v;
-        unsigned m0 = __ballot_sync(0xFFFFFFFFu, j0), m1 = __ballot_sync(0xFFFFFFFFu, j1);
-        unsigned nj0 = __popc(m0), total = nj0 + __popc(m1);
-        if (j0) my[__popc(m0 & lt)] = KoutJob{(uint32_t)v, c0, (uint32_t)lo0};
-        if (j1) my[nj0 + __popc(m1 & lt)] = KoutJob{(uint32_t)v, c1, (uint32_t)(lo0 + 1)};
+        // one job per vertex with a sampled arc, packed to the low lanes: the
+        // lane runs the vertex's unions one after the other, so the two
+        // unions of a vertex never race for its own parent entry
+        bool jv = j0 || j1;
+        unsigned mv = __ballot_sync(0xFFFFFFFFu, jv);
+        if (jv) my[__popc(mv & lt)] = make_uint4((uint32_t)v, j0 ? c0 : GC_DINF, j1 ? c1 : GC_DINF, (uint32_t)lo0);
         __syncwarp();
-        for (unsigned j = lane; j < total; j += 32) {
-            KoutJob jb = my[j];
-            if (dq.jobs) {
-                Spin fast(KOUT_FAST_STEPS, true);
-                uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, fast);
-                if (!fast.dead) continue;
-                unsigned long long slot = atomicAdd(dq.count, 1ull);
-                if (slot < dq.cap) {   // resume where the climb stopped (see Spin)
-                    dq.jobs[slot] = KoutJob{fast.at_u != GC_DINF ? fast.at_u : jb.u,
-                                            fast.at_v != GC_DINF ? fast.at_v : jb.v, jb.eid};
-                    continue;
-                }
-            }
-            Spin sp(s.cap);
-            uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
+        if (lane < (unsigned)__popc(mv)) {
+            uint4 jb = my[lane];
+            if (jb.y != GC_DINF) union_or_defer<L, F, S, SF>(s, dq, jb.x, jb.y, jb.w);
+            if (jb.z != GC_DINF) union_or_defer<L, F, S, SF>(s, dq, jb.x, jb.z, jb.w + 1);
         }
         __syncwarp();
         lo0 = lo1; hi0 = hi1; c0 = n0; c1 = n1;
