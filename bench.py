@@ -43,9 +43,9 @@ INC_TOTAL = 1 << 28
 L2_FLUSH_BYTES = 256 << 20        # > 126 MB L2
 DEFAULT_VARIANT = "kout/remcas/naive/split_one"
 # DRAM bytes (read + write) of one k_kout launch per vertex, from an ncu capture
-# of the default variant at RMAT scale 20, edge factor 16 (42.34 MB / 2^20);
-# valid while that kernel is unchanged.
-KOUT_DRAM_BYTES_PER_VERTEX = 42.339e6 / 2 ** 20
+# of the default variant at RMAT scale 20, edge factor 16 (41.984 MB read +
+# 0.383 MB written, / 2^20); valid while that kernel is unchanged.
+KOUT_DRAM_BYTES_PER_VERTEX = 42.368e6 / 2 ** 20
 
 
 def parse_variant(g, spec: str):
