@@ -116,8 +116,11 @@ typedef struct gconn_variant {
 #define GCONN_ABL_PLAIN_SAMPLE 1u
 #define GCONN_ABL_NO_VG 2u
 
-/* Fill *v with the library default (Union-Async, naive find, k-out k=2 for
- * CSR input and no sampling for COO input).  Returns GCONN_E_INVAL on NULL. */
+/* Fill *v with the library default: Union-Rem-CAS with naive find and
+ * SplitAtomicOne (the fastest finish measured on GB300 on RMAT scale 22, with
+ * and without sampling; Section 4 finds Union-Async and Union-Rem-CAS the
+ * fastest rules), k-out k=2 sampling for CSR input and no sampling for COO
+ * input.  Returns GCONN_E_INVAL on NULL. */
 gconn_status gconn_variant_default(gconn_variant* v);
 
 /* Validate a variant for an input kind (0 = COO, 1 = CSR) and a purpose
@@ -137,7 +140,7 @@ gconn_status gconn_variant_check(const gconn_variant* v, int input_kind, int pur
  *   labels : uint32[n] output, canonical min-id labels (device or host)
  *   v      : variant or NULL for the default; sampling must be NONE.
  * labels doubles as the union-find parent array while the call runs.
- * Errors: E_INVAL (null pointer with n or m > 0, n = 0xFFFFFFFF, reserved != 0),
+ * Errors: E_INVAL (null pointer with n or m > 0, n = 0xFFFFFFFF, unknown ablation bits),
  * E_UNSUPPORTED (see gconn_variant_check), E_RANGE (endpoint >= n),
  * E_NONCONVERGED, E_NOMEM, E_CUDA. */
 gconn_status gconn_cc(uint32_t n, uint64_t m, const uint32_t* edges, uint32_t* labels,

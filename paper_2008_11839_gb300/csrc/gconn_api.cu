@@ -364,9 +364,9 @@ extern "C" gconn_status gconn_variant_default(gconn_variant* v) {
     v->sample = GCONN_SAMPLE_KOUT;
     v->k = 2;
     v->hb_n = 4;
-    v->link = GCONN_LINK_ASYNC;
+    v->link = GCONN_LINK_REMCAS;   // the fastest finish measured on GB300 (RMAT scale 22)
     v->find = GCONN_FIND_NAIVE;
-    v->splice = GCONN_SPLICE_NONE;
+    v->splice = GCONN_SPLICE_SPLIT_ONE;
     v->lt_rules = GCONN_LT_PARENT | GCONN_LT_ROOTUPDATE | GCONN_LT_FULLSHORTCUT;
     v->block = 0;
     v->seed = DEFAULT_SEED;

@@ -29,7 +29,10 @@ def test_status_strings(lib):
 
 def test_variant_default_and_check(lib):
     v = g.gconn_variant_default()
-    assert v.link == b.GCONN_LINK_ASYNC and v.sample == b.GCONN_SAMPLE_KOUT and v.k == 2 and v.hb_n == 4
+    assert v.link == b.GCONN_LINK_REMCAS and v.find == b.GCONN_FIND_NAIVE and v.splice == b.GCONN_SPLICE_SPLIT_ONE
+    assert v.sample == b.GCONN_SAMPLE_KOUT and v.k == 2 and v.hb_n == 4
+    for purpose in (0, 1, 2):   # components, forest and incremental handle all accept it
+        assert g.gconn_variant_check(v, 1, purpose) == b.GCONN_OK
     assert g.gconn_variant_check(v, 1, 0) == b.GCONN_OK
     # sampling needs CSR (Section 3.3)
     assert g.gconn_variant_check(v, 0, 0) == b.GCONN_E_UNSUPPORTED
