@@ -294,7 +294,8 @@ static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_
     block_lmax<L, true>(s, seed, lmax_out, sm);
 }
 
-// Unions deferred by k_kout, re-run from their endpoints with the full cap.
+// Unions deferred by k_kout / k_hb2w, finished with the full cap from where
+// each abandoned climb stopped (see Spin).
 // Blocks of LMAX_SAMPLES threads.  With lmax_out set, the block that finishes
 // last (a counter taken after a fence; `done` must start at zero) also
 // computes L_max, one sample per thread, which needs every
