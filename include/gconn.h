@@ -240,6 +240,17 @@ gconn_status gconn_inc_query(gconn_inc* h, uint64_t q, const uint32_t* pairs, ui
 gconn_status gconn_inc_process_batch(gconn_inc* h, uint64_t b, const uint32_t* pairs, const uint8_t* is_query,
                                      uint32_t* result_bits, void* stream);
 
+/* Edge inspections of the handle's insert work, the quantity of Section 4.4's
+ * edges-inspected figure (Shiloach-Vishkin and Liu-Tarjan per batch size):
+ * a union-find finish reads each edge of an insert batch once (b per batch,
+ * and b per mixed batch of b ops); the round-based finishes re-read the whole
+ * batch every round until the labels converge (rounds x b, counted on the
+ * host, which already waits for each round's convergence flag).
+ *   *last_batch : inspections of the most recent insert or mixed batch
+ *   *total      : since the handle was created
+ * Queries are not counted.  Errors: E_INVAL on a NULL argument. */
+gconn_status gconn_inc_edges_inspected(const gconn_inc* h, uint64_t* last_batch, uint64_t* total);
+
 /* Canonical min-id labels of the current state into uint32[n] (device or host). */
 gconn_status gconn_inc_labels(gconn_inc* h, uint32_t* labels, void* stream);
 

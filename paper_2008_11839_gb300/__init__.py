@@ -87,6 +87,10 @@ class Incremental:
         gconn_inc_query(self.h, int(pairs.shape[0]), pairs, out, stream or self.stream)  # noqa: F405
         return out
 
+    def edges_inspected(self):
+        """(edge inspections of the last insert batch, total) -- Section 4.4."""
+        return gconn_inc_edges_inspected(self.h)  # noqa: F405
+
     def labels(self, device=None, stream=None):
         torch = _torch()
         out = torch.empty(self.n, dtype=torch.int32, device=device or "cuda")

@@ -129,6 +129,7 @@ _SIGS = {
     "gconn_inc_insert_batch": (_i32, [_vp, _u64, _vp, _vp]),
     "gconn_inc_query": (_i32, [_vp, _u64, _vp, _vp, _vp]),
     "gconn_inc_labels": (_i32, [_vp, _vp, _vp]),
+    "gconn_inc_edges_inspected": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "gconn_inc_process_batch": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp]),
     "gconn_inc_destroy": (_i32, [_vp]),
     "gconn_cc_csr_noalloc": (_i32, [_u32, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), _vp]),
@@ -338,6 +339,13 @@ def gconn_inc_query(h, q, pairs, connected, stream=None):
 def gconn_inc_process_batch(h, b, pairs, is_query, result_bits, stream=None):
     check(lib().gconn_inc_process_batch(h, b, ptr(pairs), ptr(is_query), ptr(result_bits), stream_handle(stream)),
           "gconn_inc_process_batch")
+
+
+def gconn_inc_edges_inspected(h):
+    """(inspections of the last insert / mixed batch, total since creation)."""
+    last, total = _u64(0), _u64(0)
+    check(lib().gconn_inc_edges_inspected(h, ctypes.byref(last), ctypes.byref(total)), "gconn_inc_edges_inspected")
+    return last.value, total.value
 
 
 def gconn_inc_labels(h, labels, stream=None):

@@ -27,9 +27,10 @@ gconn_status bfs_sample(const Variant& v, const UFState& s, const uint64_t* off,
 
 // Round-based finishes (Shiloach-Vishkin, Liu-Tarjan) over a COO list with
 // optional per-edge forest ids (NULL = the edge index).  P ends fully
-// compressed and min-rooted.
+// compressed and min-rooted.  *edge_passes (optional) receives the number of
+// kernel passes that read the whole edge list.
 gconn_status rounds_coo(const Variant& v, const UFState& s, const uint32_t* edges, const uint32_t* eids,
-                        uint64_t m, cudaStream_t st);
+                        uint64_t m, cudaStream_t st, uint32_t* edge_passes = nullptr);
 
 // The same over the arcs of the active CSR vertices gathered by k_vg.
 gconn_status rounds_csr(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,

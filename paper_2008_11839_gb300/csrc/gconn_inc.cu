@@ -21,6 +21,7 @@ struct gconn_inc {
     u64w* W;
     uint32_t* Lk;
     cudaStream_t last;
+    uint64_t inspected_last, inspected_total;   // edge inspections of the inserts (Section 4.4)
 };
 
 namespace gc {
@@ -219,11 +220,16 @@ extern "C" gconn_status gconn_inc_insert_batch(gconn_inc* h, uint64_t b, const u
     bool host = !is_device_ptr(edges);
     GC_TRY(stage_in(edges, sizeof(uint32_t) * 2 * b, st, eb, (const void**)&de));
     UFState s = handle_state(h);
+    uint64_t inspected = b;   // a union-find finish reads each edge of the batch once
     if (is_rounds_link(h->v.link)) {
-        GC_TRY(rounds_coo(h->v, s, de, nullptr, b, st));
+        uint32_t passes = 0;   // rounds re-read the whole batch until the labels converge
+        GC_TRY(rounds_coo(h->v, s, de, nullptr, b, st, &passes));
+        inspected = (uint64_t)passes * b;
     } else {
         GC_TRY(union_coo(h->v, s, de, b, 0, st));
     }
+    h->inspected_last = inspected;
+    h->inspected_total += inspected;
     if (host) return read_and_clear_err(st);
     return GCONN_OK;
 }
@@ -289,8 +295,17 @@ extern "C" gconn_status gconn_inc_process_batch(gconn_inc* h, uint64_t b, const 
         auto k = k_mixed<l, f, sp, 0>;
         return launch("mixed", k, grid_for(k, B, b), B, 0, st, (const uint2*)dp, dq, b, s, dout);
     }));
+    h->inspected_last = b;   // every op of a mixed batch is read once
+    h->inspected_total += b;
     if (host_out) GC_CUDA(cudaMemcpyAsync(result_bits, dout, sizeof(uint32_t) * words, cudaMemcpyDeviceToHost, st));
     if (host_in || host_out) return read_and_clear_err(st);
+    return GCONN_OK;
+}
+
+extern "C" gconn_status gconn_inc_edges_inspected(const gconn_inc* h, uint64_t* last_batch, uint64_t* total) {
+    if (!h || !last_batch || !total) return GCONN_E_INVAL;
+    *last_batch = h->inspected_last;
+    *total = h->inspected_total;
     return GCONN_OK;
 }
 

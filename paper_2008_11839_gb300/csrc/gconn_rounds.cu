@@ -302,7 +302,7 @@ struct RoundFlag {
 };
 
 static gconn_status run_sv(const Variant& v, const UFState& s, const uint2* E, const uint32_t* eids, uint64_t m,
-                           cudaStream_t st) {
+                           cudaStream_t st, uint32_t& passes) {
     uint32_t n = s.n;
     DevBuf prevb, msgb;
     GC_TRY(prevb.alloc(sizeof(uint32_t) * (size_t)n, st));
@@ -324,6 +324,7 @@ static gconn_status run_sv(const Variant& v, const UFState& s, const uint2* E, c
     for (uint32_t round = 0;; ++round) {
         if (round >= MAX_ROUNDS) return GCONN_E_NONCONVERGED;
         GC_TRY(flag.reset(st));
+        ++passes;
         if (sf) {
             GC_TRY(launch("sv_hook_sf", k_sv_hook_sf, grid_for(k_sv_hook_sf, 256, m), 256, 0, st, E, eids, m, n,
                           (const uint32_t*)prev, msg, s.err));
@@ -342,7 +343,7 @@ static gconn_status run_sv(const Variant& v, const UFState& s, const uint2* E, c
 }
 
 static gconn_status run_lt(const Variant& v, const UFState& s, const uint2* E_in, const uint32_t* eids, uint64_t m,
-                           cudaStream_t st) {
+                           cudaStream_t st, uint32_t& passes) {
     uint32_t n = s.n;
     int conn = v.lt_rules & 3;
     bool root_only = (v.lt_rules & GCONN_LT_ROOTUPDATE) != 0;
@@ -368,6 +369,7 @@ static gconn_status run_lt(const Variant& v, const UFState& s, const uint2* E_in
     for (uint32_t round = 0;; ++round) {
         if (round >= MAX_ROUNDS) return GCONN_E_NONCONVERGED;
         GC_TRY(flag.reset(st));
+        passes += (m ? 1u : 0u) + (alter && m ? 1u : 0u);   // connect (+ alter) read every edge
         if (m)
             GC_TRY(launch("lt_connect", k_lt_connect, grid_for(k_lt_connect, 256, m), 256, 0, st, E, eids, m, n,
                           (const uint32_t*)s.P, conn, msg, s.err));
@@ -387,12 +389,14 @@ static gconn_status run_lt(const Variant& v, const UFState& s, const uint2* E_in
     return compress_all(va, s, st);
 }
 
-static gconn_status run_lp(const Variant& v, const UFState& s, const uint2* E, uint64_t m, cudaStream_t st) {
+static gconn_status run_lp(const Variant& v, const UFState& s, const uint2* E, uint64_t m, cudaStream_t st,
+                           uint32_t& passes) {
     RoundFlag flag;
     GC_TRY(flag.init(st));
     for (uint32_t round = 0; m; ++round) {
         if (round >= MAX_ROUNDS) return GCONN_E_NONCONVERGED;
         GC_TRY(flag.reset(st));
+        ++passes;
         GC_TRY(launch("lp", k_lp, grid_for(k_lp, 256, m), 256, 0, st, E, m, s.n, s.P, flag.d(), s.err));
         bool changed = false;
         GC_TRY(flag.read(st, &changed));
@@ -403,7 +407,8 @@ static gconn_status run_lp(const Variant& v, const UFState& s, const uint2* E, u
     return compress_all(va, s, st);
 }
 
-static gconn_status run_stergiou(const Variant& v, const UFState& s, const uint2* E, uint64_t m, cudaStream_t st) {
+static gconn_status run_stergiou(const Variant& v, const UFState& s, const uint2* E, uint64_t m, cudaStream_t st,
+                                 uint32_t& passes) {
     uint32_t n = s.n;
     DevBuf prevb;
     GC_TRY(prevb.alloc(sizeof(uint32_t) * (size_t)n, st));
@@ -415,6 +420,7 @@ static gconn_status run_stergiou(const Variant& v, const UFState& s, const uint2
         if (round >= MAX_ROUNDS) return GCONN_E_NONCONVERGED;
         GC_TRY(flag.reset(st));
         GC_TRY(launch("stergiou_copy", k_copy_u32, gn, 256, 0, st, n, (const uint32_t*)s.P, prev));
+        ++passes;
         GC_TRY(launch("stergiou", k_stergiou, grid_for(k_stergiou, 256, m), 256, 0, st, E, m, n,
                       (const uint32_t*)prev, s.P, s.err));
         GC_TRY(launch("lt_shortcut", k_lt_shortcut, gn, 256, 0, st, n, s.P, flag.d()));
@@ -430,12 +436,16 @@ static gconn_status run_stergiou(const Variant& v, const UFState& s, const uint2
 }
 
 gconn_status rounds_coo(const Variant& v, const UFState& s, const uint32_t* edges, const uint32_t* eids, uint64_t m,
-                        cudaStream_t st) {
-    if (s.n == 0) return GCONN_OK;
-    if (v.link == GCONN_LINK_SV) return run_sv(v, s, (const uint2*)edges, eids, m, st);
-    if (v.link == GCONN_LINK_LP) return run_lp(v, s, (const uint2*)edges, m, st);
-    if (v.link == GCONN_LINK_STERGIOU) return run_stergiou(v, s, (const uint2*)edges, m, st);
-    return run_lt(v, s, (const uint2*)edges, eids, m, st);
+                        cudaStream_t st, uint32_t* edge_passes) {
+    uint32_t passes = 0;
+    gconn_status r = GCONN_OK;
+    if (s.n == 0) r = GCONN_OK;
+    else if (v.link == GCONN_LINK_SV) r = run_sv(v, s, (const uint2*)edges, eids, m, st, passes);
+    else if (v.link == GCONN_LINK_LP) r = run_lp(v, s, (const uint2*)edges, m, st, passes);
+    else if (v.link == GCONN_LINK_STERGIOU) r = run_stergiou(v, s, (const uint2*)edges, m, st, passes);
+    else r = run_lt(v, s, (const uint2*)edges, eids, m, st, passes);
+    if (edge_passes) *edge_passes = passes;
+    return r;
 }
 
 gconn_status rounds_csr(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,

@@ -100,6 +100,36 @@ def test_host_buffers_and_empty_batches():
     g.gconn_inc_destroy(h)
 
 
+@pytest.mark.parametrize("kw", [dict(link="sv"), dict(link="lt", lt="PRS"), dict(link="early"),
+                                dict(link="remcas", splice="split_one")], ids=_vid)
+def test_edges_inspected_per_batch(kw):
+    """Section 4.4's edges-inspected count: a union-find finish reads each
+    inserted edge once; SV and Liu-Tarjan re-read the whole batch every round,
+    and a path inserted from its far end needs several rounds."""
+    n = 4096
+    path = np.stack([np.arange(n - 1, 0, -1), np.arange(n - 2, -1, -1)], 1).astype(np.uint32)
+    h = g.Incremental(n, g.make_variant(**kw))
+    try:
+        assert h.edges_inspected() == (0, 0)
+        h.insert(dev(path))
+        g.gconn_sync()
+        last, total = h.edges_inspected()
+        b = len(path)
+        if kw["link"] in ("sv", "lt"):
+            assert last % b == 0 and last >= 2 * b, last
+        else:
+            assert last == b
+        assert total == last
+        h.insert(dev(path[:10]))
+        g.gconn_sync()
+        last2, total2 = h.edges_inspected()
+        assert total2 == total + last2 and last2 % 10 == 0 and last2 >= 10
+        lab = host_u32(h.labels())
+        assert (lab == 0).all()
+    finally:
+        h.close()
+
+
 def test_incremental_rejects_non_root_based():
     with pytest.raises(g.GconnError) as ex:
         g.gconn_inc_create(10, g.make_variant(link="lt", lt="PUS"))
