@@ -947,6 +947,43 @@ def run_ratio_sweep(args):
         torch.cuda.empty_cache()
 
 
+def run_edge_inspect(args):
+    """Section 4.4's edges-inspected figure: the first 2^24 edges of the RMAT
+    scale-24 insert stream, inserted into a fresh n = 2^24 handle in batches of
+    one size per decade 10^3 .. 10^7; per batch size and finish, the edge
+    inspections the handle counted (each edge once for union-find, every
+    round re-reads the whole batch for SV / Liu-Tarjan) and the device time."""
+    import torch
+    import paper_2008_11839_gb300 as g
+    g.build()
+    dev = torch.device("cuda", 0)
+    n = 1 << INC_N_SCALE
+    total = 1 << 24
+    perm = graphgen.permutation(n, SEED_INC, 6)
+    e = graphgen.rmat_range(INC_N_SCALE, 0, total, SEED_INC, perm=perm)
+    d_e = torch.from_numpy(e.view(np.int32)).to(dev)
+    stream = torch.cuda.current_stream()
+    for v_spec in args.inspect_variants.split(","):
+        v = parse_variant(g, "none/" + v_spec)
+        for b in [10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7]:
+            inc = g.Incremental(n, v, stream)
+            per_batch = []
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for s in range(0, total, b):
+                inc.insert(d_e[s:min(total, s + b)])
+                per_batch.append(inc.edges_inspected()[0])
+            z.record(stream)
+            z.synchronize()
+            g.gconn_sync(stream)
+            insp = inc.edges_inspected()[1]
+            inc.close()
+            print(json.dumps({"variant": v_spec, "batch": b, "batches": len(per_batch), "edges": total,
+                              "inspected": insp, "inspected_per_edge": round(insp / total, 3),
+                              "max_batch_inspections_per_edge": round(max(x / min(b, total) for x in per_batch), 3),
+                              "ms": round(a.elapsed_time(z), 3)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -978,6 +1015,9 @@ def main():
     ap.add_argument("--stats", action="store_true", help="sampling Cov / IC / Time %% per sampling method")
     ap.add_argument("--ratio-sweep", action="store_true", help="mixed batches at several insert:query ratios")
     ap.add_argument("--ratio-variants", default="early/naive,async/halve,remcas/naive/split_one")
+    ap.add_argument("--edge-inspect", action="store_true",
+                    help="edge inspections per insert batch size (SV, Liu-Tarjan PRS, union-find)")
+    ap.add_argument("--inspect-variants", default="sv,lt/PRS,early/naive")
     ap.add_argument("--stats-variants", default="kout/remcas/naive/split_one,hb/remcas/naive/split_one,"
                                                  "bfs/remcas/naive/split_one,none/remcas/naive/split_one")
     args = ap.parse_args()
@@ -997,6 +1037,9 @@ def main():
         return
     if args.ratio_sweep:
         run_ratio_sweep(args)
+        return
+    if args.edge_inspect:
+        run_edge_inspect(args)
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
