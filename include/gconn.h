@@ -19,6 +19,8 @@
  *   (each undirected edge stored as both arcs) with every row sorted
  *   ascending, as in Section 2 ("Graph Notation and Formats").
  * - Self-loops and duplicate edges are accepted and change nothing.
+ * - Edge, pair and query counts (m, b, q, count) are at most 2^60
+ *   (E_INVAL above), so every byte size fits in 64 bits.
  * - Every pointer may be device memory or host memory (pageable or pinned);
  *   the library checks each one.  Host inputs are copied to the device; host
  *   outputs are filled before the call returns.  The caller owns every buffer

@@ -80,6 +80,10 @@ void count_capture_launch();
 void prof_requeue(const ProfSink& sink);
 void prof_release(ProfSink& sink);
 
+// Largest edge / pair / query count an entry point accepts: 8-byte items, so
+// every byte count stays below 2^63.
+constexpr uint64_t GC_MAX_COUNT = 1ull << 60;
+
 // Persistent-style grid: min(ceil(work / block), resident blocks on all SMs).
 template <class K>
 unsigned grid_for(K kernel, int block, uint64_t work, size_t smem = 0) {

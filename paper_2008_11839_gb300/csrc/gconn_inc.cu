@@ -210,7 +210,7 @@ extern "C" gconn_status gconn_inc_create(uint32_t n, const gconn_variant* vin, v
 }
 
 extern "C" gconn_status gconn_inc_insert_batch(gconn_inc* h, uint64_t b, const uint32_t* edges, void* stream) {
-    if (!h || (b && !edges) || b >= (1ull << 63) || ((uintptr_t)edges & 7u)) return GCONN_E_INVAL;
+    if (!h || (b && !edges) || b > GC_MAX_COUNT || ((uintptr_t)edges & 7u)) return GCONN_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     h->last = st;
     if (b == 0) return GCONN_OK;
@@ -236,7 +236,7 @@ extern "C" gconn_status gconn_inc_insert_batch(gconn_inc* h, uint64_t b, const u
 
 extern "C" gconn_status gconn_inc_query(gconn_inc* h, uint64_t q, const uint32_t* pairs, uint8_t* connected,
                                         void* stream) {
-    if (!h || (q && (!pairs || !connected)) || q >= (1ull << 63) || ((uintptr_t)pairs & 7u)) return GCONN_E_INVAL;
+    if (!h || (q && (!pairs || !connected)) || q > GC_MAX_COUNT || ((uintptr_t)pairs & 7u)) return GCONN_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     h->last = st;
     if (q == 0) return GCONN_OK;
@@ -258,7 +258,7 @@ extern "C" gconn_status gconn_inc_query(gconn_inc* h, uint64_t q, const uint32_t
 
 extern "C" gconn_status gconn_inc_process_batch(gconn_inc* h, uint64_t b, const uint32_t* pairs,
                                                 const uint8_t* is_query, uint32_t* result_bits, void* stream) {
-    if (!h || (b && (!pairs || !is_query || !result_bits)) || b >= (1ull << 63) || ((uintptr_t)pairs & 7u) ||
+    if (!h || (b && (!pairs || !is_query || !result_bits)) || b > GC_MAX_COUNT || ((uintptr_t)pairs & 7u) ||
         ((uintptr_t)result_bits & 3u))
         return GCONN_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;

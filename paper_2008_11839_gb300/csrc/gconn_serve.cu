@@ -508,7 +508,7 @@ extern "C" gconn_status gconn_server_open_session(gconn_server* S, uint32_t n, c
 extern "C" gconn_status gconn_server_submit(gconn_server* S, uint32_t session, int op, uint64_t count,
                                             const uint32_t* pairs, uint8_t* result, uint64_t* ticket) {
     if (!S || !ticket || (op != GCONN_OP_INSERT && op != GCONN_OP_QUERY)) return GCONN_E_INVAL;
-    if (count && !pairs) return GCONN_E_INVAL;
+    if ((count && !pairs) || count > GC_MAX_COUNT) return GCONN_E_INVAL;
     if (op == GCONN_OP_QUERY && count && !result) return GCONN_E_INVAL;
     std::lock_guard<std::mutex> lk(S->mu);
     auto it = S->sessions.find(session);

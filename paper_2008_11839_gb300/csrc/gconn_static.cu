@@ -357,7 +357,7 @@ static gconn_status static_run(uint32_t n, uint64_t m, const uint32_t* edges, co
     if (csr && !off) return GCONN_E_INVAL;
     if (!csr && m && !edges) return GCONN_E_INVAL;
     if (!csr && want_forest && m >= 0xFFFFFFFFull) return GCONN_E_INVAL;
-    if (!csr && m >= (1ull << 63)) return GCONN_E_INVAL;
+    if (!csr && m > GC_MAX_COUNT) return GCONN_E_INVAL;
     // edges are read as 8-byte pairs, offsets as 8-byte words
     if (!csr && edges && ((uintptr_t)edges & 7u)) return GCONN_E_INVAL;
     if (csr && ((uintptr_t)off & 7u)) return GCONN_E_INVAL;

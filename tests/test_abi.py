@@ -109,3 +109,23 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(b, "_lib", None)
     with pytest.raises(b.GconnUnavailable):
         b.lib()
+
+
+def test_argument_checks_precede_device_work(lib):
+    """Malformed arguments are rejected on the host before any CUDA call, so
+    these run without a GPU: counts above 2^60, the reserved n, unaligned
+    edge arrays and null outputs all give E_INVAL."""
+    import numpy as np
+    e = np.zeros((4, 2), np.uint32)
+    lab = np.zeros(10, np.uint32)
+    cases = [
+        lambda: g.gconn_cc(10, (1 << 60) + 1, e, lab),                     # count limit
+        lambda: g.gconn_cc(0xFFFFFFFF, 0, None, lab),                      # reserved vertex count
+        lambda: g.gconn_cc(10, 3, e.reshape(-1)[1:7], lab),                # edges not 8-byte aligned
+        lambda: g.gconn_cc(10, 4, e, None),                                # no output
+        lambda: g.gconn_spanning_forest(10, 1 << 32, e, lab, lab, None),   # forest ids above 32 bits
+    ]
+    for call in cases:
+        with pytest.raises(g.GconnError) as ex:
+            call()
+        assert ex.value.status == g.GCONN_E_INVAL
