@@ -272,7 +272,9 @@ gconn_status gconn_inc_destroy(gconn_inc* h);
  * Requests use HOST buffers, which must stay valid until gconn_server_wait
  * returns for that ticket; answers are written to `result` (uint8 per pair).
  * gconn_server_wait blocks until the request completed and gives its latency
- * (submit to answer available, host clock).  All calls are thread-safe. */
+ * (submit to answer available, host clock); each ticket is waited for once
+ * (a second wait, or a ticket never issued, returns E_INVAL).  All calls are
+ * thread-safe. */
 enum { GCONN_OP_INSERT = 0, GCONN_OP_QUERY = 1 };
 typedef struct gconn_server_config {
     uint64_t device_budget_bytes;  /* staging bytes allowed in flight (default 4 GiB) */

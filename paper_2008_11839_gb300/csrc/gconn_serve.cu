@@ -28,6 +28,7 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <set>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -193,6 +194,7 @@ struct gconn_server {
         double latency_ms;
     };
     std::map<uint64_t, Done> done;
+    std::set<uint64_t> unclaimed;   // issued tickets no gconn_server_wait has taken yet
     uint64_t launches = 0, steps = 0, requests_done = 0;
 };
 
@@ -515,6 +517,7 @@ extern "C" gconn_status gconn_server_submit(gconn_server* S, uint32_t session, i
     if (it == S->sessions.end() || it->second.closing) return GCONN_E_INVAL;
     Request r{S->next_ticket++, session, op, count, pairs, result, Clock::now()};
     *ticket = r.ticket;
+    S->unclaimed.insert(r.ticket);
     if (count == 0) {
         S->done[r.ticket] = {GCONN_OK, 0.0};
         return GCONN_OK;
@@ -527,7 +530,9 @@ extern "C" gconn_status gconn_server_submit(gconn_server* S, uint32_t session, i
 extern "C" gconn_status gconn_server_wait(gconn_server* S, uint64_t ticket, double* latency_ms) {
     if (!S) return GCONN_E_INVAL;
     std::unique_lock<std::mutex> lk(S->mu);
-    if (ticket == 0 || ticket >= S->next_ticket) return GCONN_E_INVAL;
+    // each ticket is waited for once: a second wait (or one for a ticket never
+    // issued) is an error instead of a wait that no completion would end
+    if (S->unclaimed.erase(ticket) == 0) return GCONN_E_INVAL;
     S->cv_done.wait(lk, [&] { return S->done.count(ticket) > 0; });
     auto d = S->done[ticket];
     S->done.erase(ticket);

@@ -148,5 +148,9 @@ def test_errors():
     assert ex.value.status == g.GCONN_E_RANGE
     ok = g.gconn_server_submit(srv, sid, g.GCONN_OP_INSERT, 1, np.array([[0, 99]], np.uint32))
     g.gconn_server_wait(srv, ok)
+    for bad in (ok, ok + 1000):   # a ticket is waited for once; unknown tickets are refused, not waited on
+        with pytest.raises(g.GconnError) as ex:
+            g.gconn_server_wait(srv, bad)
+        assert ex.value.status == g.GCONN_E_INVAL
     g.gconn_server_close_session(srv, sid)
     g.gconn_server_destroy(srv)
