@@ -432,19 +432,7 @@ static __global__ void __launch_bounds__(256) k_hb2w(const uint64_t* __restrict_
         __syncwarp();
         for (unsigned j = lane; j < total; j += 32) {
             KoutJob jb = my[j];
-            if (dq.jobs) {
-                Spin fast(KOUT_FAST_STEPS, true);
-                uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, fast);
-                if (!fast.dead) continue;
-                unsigned long long slot = atomicAdd(dq.count, 1ull);
-                if (slot < dq.cap) {   // resume where the climb stopped (see Spin)
-                    dq.jobs[slot] = KoutJob{fast.at_u != GC_DINF ? fast.at_u : jb.u,
-                                            fast.at_v != GC_DINF ? fast.at_v : jb.v, jb.eid};
-                    continue;
-                }
-            }
-            Spin sp(s.cap);
-            uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
+            union_or_defer<L, F, S, SF>(s, dq, jb.u, jb.v, jb.eid);
         }
         __syncwarp();
         lo0 = lo1; hi0 = hi1;
