@@ -148,3 +148,55 @@ def test_label_propagation_rounds_track_diameter():
     path = [(i, i + 1) for i in reversed(range(k - 1))]   # far end first: one hop per round
     lab, rounds = mr.label_propagation(k, path)
     assert lab == [0] * k and rounds >= k - 1
+
+
+def _same_set_lockstep(x, y, P):
+    """The GPU query walk (query batches and serving query segments under the
+    naive find): both endpoints climb one step per iteration, and a walk that
+    stands on a root above the other walk's vertex answers "different"."""
+    while x != y:
+        px, py = P[x], P[y]
+        rx, ry = px == x, py == y
+        if (rx and (ry or y < x)) or (ry and x < y):
+            return False
+        x, y = px, py
+    return True
+
+
+def _same_set_lockstep_wrong(x, y, P):   # planted: the early exit tests the wrong side
+    while x != y:
+        px, py = P[x], P[y]
+        rx, ry = px == x, py == y
+        if (rx and (ry or y > x)) or (ry and x > y):
+            return False
+        x, y = px, py
+    return True
+
+
+LOCKSTEP_RULES = [("async", "naive", "splice"), ("hooks", "naive", "splice"), ("early", "naive", "splice"),
+                  ("remcas", "naive", "split_one"), ("remcas", "naive", "splice"), ("remlock", "naive", "halve_one"),
+                  ("afforest", "naive", "splice"), ("eclcc", "naive", "splice")]
+
+
+@pytest.mark.parametrize("link,find,splice", LOCKSTEP_RULES)
+def test_lockstep_query_equals_root_comparison(link, find, splice):
+    """Every non-JTB rule keeps P[v] <= v, so a root is the smallest vertex of
+    its tree; on the forests these rules build (whole graphs and prefixes of
+    their edge lists), the lock-step walk answers exactly Find(u) == Find(v)
+    for every pair, and the planted wrong early exit is caught."""
+    caught = False
+    for n, e in GRAPHS[:4]:
+        for cut in (len(e) // 3, len(e)):
+            uf = mr.UF(n, link=link, find=find, splice=splice)
+            for u, v in e[:cut].tolist():
+                if u != v:
+                    uf.union(u, v)
+            P = uf.P
+            assert all(P[v] <= v for v in range(n))
+            roots = [uf.root(v) for v in range(n)]
+            for x in range(n):
+                for y in range(n):
+                    want = roots[x] == roots[y]
+                    assert _same_set_lockstep(x, y, P) == want, (x, y)
+                    caught |= _same_set_lockstep_wrong(x, y, P) != want
+    assert caught
