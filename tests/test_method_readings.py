@@ -200,3 +200,61 @@ def test_lockstep_query_equals_root_comparison(link, find, splice):
                     assert _same_set_lockstep(x, y, P) == want, (x, y)
                     caught |= _same_set_lockstep_wrong(x, y, P) != want
     assert caught
+
+
+def _rem_cas_budget(u, v, P, splice, steps):
+    """Union-Rem-CAS (Algorithm 11) that gives up after `steps` splice steps
+    and returns the pair its climb stood on (None once linked or joined)."""
+    ru, rv = u, v
+    while P[ru] != P[rv]:
+        if P[ru] < P[rv]:
+            ru, rv = rv, ru
+        if ru == P[ru] and mr.cas(P, ru, ru, P[rv]):
+            return None
+        ru = splice(ru, rv, P)
+        steps -= 1
+        if steps == 0:
+            return ru, rv
+    return None
+
+
+def _labels_of(P):
+    roots = [mr.find_naive(v, P) for v in range(len(P))]
+    low = {}
+    for v, r in enumerate(roots):
+        low.setdefault(r, v)
+    return np.array([low[r] for r in roots], np.uint32)
+
+
+@pytest.mark.parametrize("splice", ["split_one", "halve_one", "splice"])
+def test_abandoned_union_resumes_from_its_current_pair(splice):
+    """R34: a union abandoned after a few steps and finished later must resume
+    from the pair its climb stood on.  With SpliceAtomic, restarting from the
+    endpoints can drop part of a set (the splice already moved a subtree of
+    u's set into v's tree, so u and v look joined while the rest of u's set is
+    not linked): the planted restart is caught there, and resuming is exact
+    for every splice rule."""
+    rng = np.random.default_rng(5)
+    lost = False
+    for trial in range(60):
+        n = int(rng.integers(8, 40))
+        e = rng.integers(0, n, size=(int(rng.integers(n, 3 * n)), 2)).astype(np.uint32)
+        want = oracle.cc_uf(n, e)
+        budgets = rng.integers(1, 3, size=len(e))
+        for resume in (True, False):
+            P = list(range(n))
+            later = []
+            for (u, v), b in zip(e.tolist(), budgets.tolist()):
+                if u == v:
+                    continue
+                stop = _rem_cas_budget(u, v, P, mr.SPLICES[splice], b)
+                if stop is not None:
+                    later.append(stop if resume else (u, v))
+            for u, v in later:
+                mr.union_rem_cas(u, v, P, mr.find_naive, mr.SPLICES[splice])
+            same = (_labels_of(P) == want).all()
+            if resume:
+                assert same, (trial, splice)
+            else:
+                lost |= not same
+    assert lost == (splice == "splice")
