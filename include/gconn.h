@@ -345,7 +345,8 @@ typedef struct gconn_batch_tune {
 
 gconn_status gconn_batch_tune_default(gconn_batch_tune* t);
 
-/* One-shot: plan, run and wait.  Errors: E_INVAL (offsets not monotone, host
+/* One-shot: plan, run and wait.  Errors: E_INVAL (offsets not monotone, a
+ * graph with more than 0xFFFFFFFE vertices, more than 2^60 edges in all, host
  * edges / labels, misaligned edges, bad tune table), E_UNSUPPORTED, E_NOMEM,
  * E_CUDA; E_RANGE (local endpoint >= n_g) via gconn_sync. */
 gconn_status gconn_cc_batched(uint32_t G, const uint64_t* vtx_off, const uint64_t* edge_off,

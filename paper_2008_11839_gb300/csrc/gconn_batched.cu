@@ -301,9 +301,12 @@ static gconn_status batch_build(uint32_t G, const uint64_t* vtx_off, const uint6
     } else {
         memcpy(b->heo.data(), edge_off, ob);
     }
-    for (uint32_t g = 0; g < G; ++g)
+    for (uint32_t g = 0; g < G; ++g) {
         if (b->hvo[g + 1] < b->hvo[g] || b->heo[g + 1] < b->heo[g]) return fail(GCONN_E_INVAL);
+        if (b->hvo[g + 1] - b->hvo[g] > 0xFFFFFFFEull) return fail(GCONN_E_INVAL);   // local ids are uint32
+    }
     uint64_t total_n = b->hvo[G], total_m = b->heo[G];
+    if (total_m - b->heo[0] > GC_MAX_COUNT) return fail(GCONN_E_INVAL);
     if ((total_m && !edges) || (total_n && !labels)) return fail(GCONN_E_INVAL);
     if (total_m && (!is_device_ptr(edges) || ((uintptr_t)edges & 7u))) return fail(GCONN_E_INVAL);
     if (total_n && !is_device_ptr(labels)) return fail(GCONN_E_INVAL);
