@@ -154,3 +154,37 @@ def test_errors():
         assert ex.value.status == g.GCONN_E_INVAL
     g.gconn_server_close_session(srv, sid)
     g.gconn_server_destroy(srv)
+
+
+def test_closing_one_session_leaves_others_unaffected():
+    """A client that leaves mid-stream: closing session A while both sessions
+    still have requests queued finishes A's requests first (their answers
+    stay exact), B's answers and labels equal the oracle's, and A no longer
+    accepts requests."""
+    (na, sa, kwa), (nb, sb, kwb) = SESSIONS[0], SESSIONS[2]
+    ra, rb = _session_stream(na, sa), _session_stream(nb, sb)
+    ref_a, ref_b = _oracle_answers(na, ra), _oracle_answers(nb, rb)
+    srv = g.gconn_server_create()
+    a = g.gconn_server_open_session(srv, na, g.make_variant(**kwa))
+    b = g.gconn_server_open_session(srv, nb, g.make_variant(**kwb))
+
+    def submit(sid, reqs):
+        out = []
+        for op, arr in reqs:
+            res = np.empty(len(arr), np.uint8) if op == g.GCONN_OP_QUERY else None
+            out.append((g.gconn_server_submit(srv, sid, op, len(arr), arr, res), res))
+        return out
+    ta, tb = submit(a, ra), submit(b, rb)
+    g.gconn_server_close_session(srv, a)
+    with pytest.raises(g.GconnError) as ex:
+        g.gconn_server_submit(srv, a, g.GCONN_OP_INSERT, 1, np.array([[0, 1]], np.uint32))
+    assert ex.value.status == g.GCONN_E_INVAL
+    for tickets, ref in ((ta, ref_a), (tb, ref_b)):
+        for (t, res), want in zip(tickets, ref[0]):
+            g.gconn_server_wait(srv, t)
+            if want is not None:
+                assert (res == want).all()
+    lab = np.empty(nb, np.uint32)
+    g.gconn_server_labels(srv, b, lab)
+    assert (lab == ref_b[1]).all()
+    g.gconn_server_destroy(srv)
