@@ -113,3 +113,22 @@ def test_ba_endpoint_copying_and_shape():
     big = graphgen.ba(100_000, 4, 5)
     deg = np.bincount(big.ravel(), minlength=100_000)
     assert deg.max() > 20 * deg.mean()          # hubs: early vertices gather ~ d sqrt(n / i) edges
+
+
+def test_generator_outputs_are_stable():
+    """Every generator's output for a fixed seed, pinned by hash: the inputs the
+    tests and the benchmark use must not drift between builds or machines (the
+    C code depends on no platform integer width beyond uint64 / __int128)."""
+    import hashlib
+
+    def h(a):
+        return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()[:16]
+    assert h(graphgen.er(1000, 5000, 1)) == "86c9ca8de9ccff49"
+    assert h(graphgen.rmat(12, 5000, 3)) == "6de8fdc2613d7e8a"
+    assert h(graphgen.permutation(1 << 12, 3, 6)) == "5e4ce5916122c76a"
+    n, e = graphgen.grid_paths(16, 0.05, 4, 64, 7)
+    assert n == 512 and h(e) == "d8ffa09ca42169d2"
+    assert h(graphgen.pairs_range(1000, 0, 4000, 9)) == "403c3d91c30db885"
+    assert h(graphgen.ba(2000, 4, 11)) == "45108feb8c446438"
+    assert [h(x) for x in graphgen.batched(8, 5, nmin=16, nmax=256)] == \
+        ["dccbdf458f5f2de6", "04b766d1c5298541", "d29b29b0103d69c9"]
