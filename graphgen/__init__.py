@@ -34,10 +34,13 @@ GRAPH500 = (0.57, 0.19, 0.19)
 
 
 def build(force: bool = False) -> str:
-    """Compile graphgen.c into libgraphgen.so next to it (gcc, OpenMP)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile graphgen.c into libgraphgen.so next to it (gcc, OpenMP).  No
+    fused multiply-add contraction: the batched sizes' floating-point steps
+    round the same way on every machine (aarch64 gcc contracts by default)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC),
+                                                                         os.path.getmtime(__file__)):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=gnu11",
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-std=gnu11",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
