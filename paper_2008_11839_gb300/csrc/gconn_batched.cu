@@ -39,7 +39,7 @@ __device__ __forceinline__ uint32_t sm_cas(volatile uint16_t* P, uint32_t i, uin
 
 template <int R>
 __device__ __forceinline__ uint32_t sm_find(volatile uint16_t* P, uint32_t u, uint32_t& left) {
-    if (R == BR_ASYNC_HALVE) {
+    if constexpr (R == BR_ASYNC_HALVE) {
         while (left) {
             uint32_t v = sm_ld(P, u), w = sm_ld(P, v);
             if (v == w) return v;
@@ -48,14 +48,15 @@ __device__ __forceinline__ uint32_t sm_find(volatile uint16_t* P, uint32_t u, ui
             --left;
         }
         return u;
+    } else {
+        while (left) {
+            uint32_t p = sm_ld(P, u);
+            if (p == u) return u;
+            u = p;
+            --left;
+        }
+        return u;
     }
-    while (left) {
-        uint32_t p = sm_ld(P, u);
-        if (p == u) return u;
-        u = p;
-        --left;
-    }
-    return u;
 }
 
 // One union in shared memory: Union-Async (naive or halving find) or

@@ -372,30 +372,31 @@ __device__ __forceinline__ uint32_t jtb_priority(uint32_t seed, uint32_t v) {
 template <int F>
 __device__ __forceinline__ uint32_t jtb_find(const UFState& s, uint32_t u, Spin& sp) {
     u64w* W = s.W;
-    if (F != FD_TWOTRY) {  // FindSimple
+    if constexpr (F != FD_TWOTRY) {  // FindSimple
         while (true) {
             uint32_t p = wpar(ldw(W, u));
             if (p == u) return u;
             u = p;
             if (!sp.step(s)) return u;
         }
-    }
-    while (true) {  // FindTwoTrySplit: up to two split attempts per step
-        u64w wu = ldw(W, u);
-        uint32_t v = wpar(wu);
-        if (v == u) return u;
-        uint32_t w = wpar(ldw(W, v));
-        if (w == v) return v;
-        for (int t = 0; t < 2; ++t) {
-            u64w old = atomicCAS(W + u, wu, wmake(wrank(wu), w));
-            if (old == wu) break;
-            wu = old;
-            v = wpar(wu);
-            w = wpar(ldw(W, v));
-            if (w == v) break;
+    } else {
+        while (true) {  // FindTwoTrySplit: up to two split attempts per step
+            u64w wu = ldw(W, u);
+            uint32_t v = wpar(wu);
+            if (v == u) return u;
+            uint32_t w = wpar(ldw(W, v));
+            if (w == v) return v;
+            for (int t = 0; t < 2; ++t) {
+                u64w old = atomicCAS(W + u, wu, wmake(wrank(wu), w));
+                if (old == wu) break;
+                wu = old;
+                v = wpar(wu);
+                w = wpar(ldw(W, v));
+                if (w == v) break;
+            }
+            u = v;
+            if (!sp.step(s)) return u;
         }
-        u = v;
-        if (!sp.step(s)) return u;
     }
 }
 
