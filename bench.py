@@ -45,7 +45,9 @@ DEFAULT_VARIANT = "kout/remcas/naive/split_one"
 # DRAM bytes (read + write) of one k_kout launch per vertex, from an ncu capture
 # of the default variant at RMAT scale 20, edge factor 16 (41.984 MB read +
 # 0.383 MB written, / 2^20); valid while that kernel is unchanged.
-KOUT_DRAM_BYTES_PER_VERTEX = 42.368e6 / 2 ** 20
+KOUT_DRAM_BYTES_PER_VERTEX = None     # re-captured after the uint32-offset k_kout
+KOUT_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_kout launch at RMAT scale 20 "
+                    "(same variant and edge factor), scaled by the vertex count")
 
 
 def parse_variant(g, spec: str):
@@ -150,20 +152,39 @@ def inc_batches(seed: int):
 
 # ------------------------------------------------------------ roofline
 def alg_bytes(name: str, st: dict):
-    """Algorithmic DRAM bytes of one launch of a kernel (what it must move at
-    least once; random-access amplification not counted)."""
+    """Algorithmic DRAM bytes of one launch of a kernel: what the executed
+    variant must move at least once, by the per-unit terms of the method's
+    measurement model (random-access sector amplification not counted, nor the
+    arcs that sampling avoids):
+      init 4n (P[v] = v); k-out sampling 4(n+1) + 4kn (uint32 offsets, k
+      columns per vertex); vertex gathering 4n (one read of the labels);
+      CSR finish 4 * (arcs of active vertices) + 8 * (active vertices);
+      finalisation 8n (read + write); full compression 8n; COO finish 8m.
+    Kernels outside the model (the deferred-union retry) count 0."""
     n = st["n"]
-    if name == "kout":
-        return 8 * (n + 1) + 4 * st["kout_arcs"] + 4 * n
-    if name in ("compress", "finalize"):
-        return 8 * n
     if name == "init":
         return 4 * n
+    if name == "kout":
+        return 4 * (n + 1) + 4 * st.get("k", 2) * n
     if name == "vg":
-        return 8 * (n + 1) + 4 * n
+        return 4 * n
+    if name == "finish":
+        return 4 * st.get("active_arcs", 0) + 8 * st.get("active_vertices", 0)
+    if name in ("compress", "finalize"):
+        return 8 * n
+    if name == "tail":           # gathering + finish + finalisation in one launch
+        return 4 * n + 4 * st.get("active_arcs", 0) + 8 * st.get("active_vertices", 0) + 8 * n
     if name == "union_coo":
-        return 8 * st["m"] + 4 * n
+        return 8 * st["m"]
     return None
+
+
+def roofline(bytes_, ms, hbm, peak_src, **extra):
+    ach = bytes_ / (ms * 1e-3) / 1e9
+    d = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+         "alg_bytes": int(bytes_), "peak_source": peak_src}
+    d.update(extra)
+    return d
 
 
 def profile_table(g):
@@ -220,13 +241,22 @@ def run_ours(args, rank, world, local_rank):
     n, e, off, cols, seed = make_static_input(rank, args.scale, args.edges)
     M = args.edges
     deg = np.diff(off).astype(np.int64)
-    st = {"n": n, "m": M, "narcs": int(off[-1]), "kout_arcs": int(np.minimum(deg, 2).sum())}
+    st = {"n": n, "m": M, "narcs": int(off[-1]), "kout_arcs": int(np.minimum(deg, 2).sum()), "k": 2}
     d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+    off32 = off.astype(np.uint32)                      # 2m < 2^32 arcs: uint32 offsets
+    d_off32 = torch.from_numpy(off32.view(np.int32)).to(dev)
     d_cols = torch.from_numpy(cols.view(np.int32)).to(dev)
     labels = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     v = parse_variant(g, args.variant)
     stream = torch.cuda.current_stream()
+    # the finish's algorithmic bytes need the active set that sampling leaves:
+    # one untimed counting pass of the same variant and seed
+    try:
+        cs = g.gconn_cc_csr_stats(n, d_off, d_cols, labels, v, stream)
+        st["active_vertices"], st["active_arcs"] = int(cs.active_vertices), int(cs.active_arcs)
+    except g.GconnError:
+        pass
     # One static pass is captured once into a CUDA graph.  Every timed kernel
     # adds two event-record nodes, and each serialises the replay for a few
     # microseconds (and breaks the programmatic-launch overlap around it), so
@@ -237,10 +267,10 @@ def run_ours(args, rank, world, local_rank):
     # region, for that kernel's live duration (the roofline).
     def make_plan(select, profiled=True):
         if not profiled:
-            return g.gconn_plan_create_cc_csr(n, d_off, d_cols, labels, v)
+            return g.gconn_plan_create_cc_csr32(n, d_off32, d_cols, labels, v)
         g.gconn_profile_select(select)
         g.gconn_profile_enable(True)
-        p = g.gconn_plan_create_cc_csr(n, d_off, d_cols, labels, v)
+        p = g.gconn_plan_create_cc_csr32(n, d_off32, d_cols, labels, v)
         g.gconn_profile_enable(False)
         g.gconn_profile_select(None)
         return p
@@ -281,8 +311,8 @@ def run_ours(args, rank, world, local_rank):
     g.gconn_sync(stream)
     g.gconn_profile_sync()
 
-    # parity of the benchmarked configuration against the oracle's labels is
-    # covered by the tests; here a cheap invariant check guards the numbers
+    # a cheap invariant check here; the labels of the last timed pass are
+    # compared bit for bit with the oracle's in the CPU-baseline leg
     lab = labels.cpu().numpy().view(np.uint32)
     ok = bool((lab <= np.arange(n, dtype=np.uint32)).all() and (lab[lab] == lab).all()
               and (lab[e[:4096, 0]] == lab[e[:4096, 1]]).all())
@@ -306,6 +336,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     launches = g.gconn_launch_count() - launches0
+    lab_timed = labels.cpu().numpy().view(np.uint32).copy()   # the last timed pass's labels
     for i in range(args.steps):      # the dominant kernel's live duration, same workload
         flush.fill_(i + 2000)
         g.gconn_plan_run(plan_dom, stream)
@@ -338,25 +369,21 @@ def run_ours(args, rank, world, local_rank):
         per_launch_ms = dom[1]["ms"] / max(dom[1]["launches"], 1)
         b = alg_bytes(dom[0], st)
         if b is not None:
-            ach = b / (per_launch_ms * 1e-3) / 1e9
             traffic, tsrc = None, None
-            if dom[0] == "kout" and args.variant == DEFAULT_VARIANT and args.edges == 16 * n:
+            if dom[0] == "kout" and args.variant == DEFAULT_VARIANT and args.edges == 16 * n and KOUT_DRAM_BYTES_PER_VERTEX:
                 traffic = int(KOUT_DRAM_BYTES_PER_VERTEX * n)
-                tsrc = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_kout launch at RMAT scale 20 "
-                        "(same variant and edge factor), scaled by the vertex count")
-            roof = {"kernel": dom[0], "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                    "frac": round(ach / hbm, 4), "traffic": traffic, "traffic_source": tsrc,
-                    "peak_source": peak_src, "alg_bytes_per_launch": b, "avg_launch_ms": round(per_launch_ms, 5)}
+                tsrc = KOUT_DRAM_SOURCE
+            roof = roofline(b, per_launch_ms, hbm, peak_src, kernel=dom[0], traffic=traffic, traffic_source=tsrc,
+                            alg_bytes_per_launch=b, avg_launch_ms=round(per_launch_ms, 5),
+                            bytes_model="4(n+1) + 4kn (k = 2)" if dom[0] == "kout" else None)
     step_share = {k: round(vv["ms"] / max(sum(x["ms"] for x in prof_all.values()), 1e-9), 4)
                   for k, vv in prof_all.items()}
     kernel_us = {k: round(1e3 * vv["ms"] / max(vv["launches"], 1), 2) for k, vv in prof_all.items()}
-    # whole-pass algorithmic bytes (the kernels that stream per-vertex data;
-    # after sampling the finish's active-set bytes are negligible) and the
-    # input-equivalent bandwidth (8m + 12n) / t, which sampling lets exceed HBM
+    # whole-pass algorithmic bytes (every kernel of the pass by the same model)
+    # and the input-equivalent bandwidth (8m + 12n) / t, which sampling lets exceed HBM
     pass_b = sum(alg_bytes(name, st) or 0 for name in prof_all)
-    pass_gbs = pass_b / (ms * 1e-3) / 1e9
-    pass_roof = {"alg_bytes": pass_b, "kernels": [x for x in prof_all if alg_bytes(x, st)],
-                 "achieved": round(pass_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(pass_gbs / hbm, 4)}
+    pass_roof = roofline(pass_b, ms, hbm, peak_src, kernels=[x for x in prof_all if alg_bytes(x, st)],
+                         terms={x: alg_bytes(x, st) for x in prof_all if alg_bytes(x, st)})
     input_eq = {"value": round((8 * M + 12 * n) / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
                 "definition": "(8 m + 12 n) / step time: the bytes an unsampled pass would stream"}
 
@@ -368,7 +395,7 @@ def run_ours(args, rank, world, local_rank):
               "data": "synthetic", "gpu_launches": int(launches), "labels_invariant_ok": ok,
               "config": {"workload": f"static_cc_rmat_s{args.scale}", "n": n, "m_undirected": M,
                          "arcs_csr": st["narcs"], "rmat_abcd": [0.57, 0.19, 0.19, 0.05], "seed": seed,
-                         "variant": args.variant, "input": "CSR (u64 offsets, u32 cols), resident",
+                         "variant": args.variant, "input": "CSR (u32 offsets, u32 cols), resident",
                          "launch": "one captured CUDA graph per step (gconn_plan_run)",
                          "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
               "roofline": roof, "pass_roofline": pass_roof, "input_equivalent_bw": input_eq,
@@ -383,40 +410,181 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the C ABI with pinned host buffers
     if rank == 0 and not args.no_e2e:
-        h_off = torch.from_numpy(off.view(np.int64)).pin_memory()
+        h_off = torch.from_numpy(off32.view(np.int32)).pin_memory()
         h_cols = torch.from_numpy(cols.view(np.int32)).pin_memory()
         h_lab = torch.empty(n, dtype=torch.int32).pin_memory()
         for _ in range(2):
-            g.gconn_cc_csr(n, h_off, h_cols, h_lab, v, stream)
+            g.gconn_cc_csr32(n, h_off, h_cols, h_lab, v, stream)
         tt = []
         for i in range(args.steps):
             flush.fill_(i)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            g.gconn_cc_csr(n, h_off, h_cols, h_lab, v, stream)   # H2D + kernels + D2H + sync
+            g.gconn_cc_csr32(n, h_off, h_cols, h_lab, v, stream)   # H2D + kernels + D2H + sync
             tt.append(time.perf_counter() - t1)
         e2e_s = float(np.mean(tt))
         result["e2e"] = {"value": M / e2e_s, "unit": "edges/s",
-                         "h2d_bytes_per_step": int(off.nbytes + cols.nbytes),
+                         "h2d_bytes_per_step": int(off32.nbytes + cols.nbytes),
                          "d2h_bytes_per_step": int(4 * n), "ms_per_step": round(e2e_s * 1e3, 4)}
 
+    legs = {"rmat_s22": (n, e, lab_timed)}      # final labels, checked against the oracle below
+    roof_args = (hbm, peak_src)
+    if rank == 0 and not args.no_c1:
+        result["static_cc_er_c1"], legs["er_c1"] = run_c1(g, torch, dev, stream, args, flush, *roof_args)
+    if rank == 0 and not args.no_c3:
+        result["static_cc_grid_paths"], legs["grid_paths"] = run_c3(g, torch, dev, stream, args, flush, *roof_args)
     if rank == 0 and not args.no_incremental:
-        result["incremental"] = run_incremental(g, torch, dev, stream, args)
+        result["incremental"] = run_incremental(g, torch, dev, stream, args, *roof_args)
     if rank == 0 and not args.no_batched:
-        result["batched"] = run_batched(g, torch, dev, stream, args)
+        result["batched"] = run_batched(g, torch, dev, stream, args, *roof_args)
     if rank == 0 and not args.no_forest:
-        result["spanning_forest"] = run_forest(g, torch, dev, stream, args, n, M, d_off, d_cols, labels, flush)
+        result["spanning_forest"] = run_forest(g, torch, dev, stream, args, n, M, d_off32, d_cols, labels, flush, st,
+                                               *roof_args)
     if rank == 0 and not args.no_serving:
         result["serving"] = run_serving(g, torch, args)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(n, e, args.cpu_seconds)
         result["cpu_multicore"] = cpu_multicore(n, M, off, cols, args.scale)
+        checks = oracle_label_checks(legs)
+        result["labels_equal_oracle"] = checks.get("rmat_s22")
+        result["oracle_label_checks"] = checks
     if dist:
         dist.destroy_process_group()
     return result
 
 
-def run_incremental(g, torch, dev, stream, args):
+def _time_passes(torch, stream, run, flush, warmup, steps, seed_base):
+    """Device time of `run` (one pass), CUDA events on the launching stream,
+    L2 flushed before every pass; returns the per-pass milliseconds."""
+    for i in range(warmup):
+        flush.fill_(seed_base + i)
+        run()
+    torch.cuda.synchronize()
+    ts = []
+    for i in range(steps):
+        flush.fill_(seed_base + 100 + i)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return ts
+
+
+def _pass_runner(g, plan_fn, direct_fn):
+    """A captured plan where the variant allows one, else direct C-ABI calls."""
+    try:
+        plan = plan_fn()
+    except g.GconnError:
+        plan = None
+    if plan is not None:
+        return plan, (lambda st: g.gconn_plan_run(plan, st)), "captured plan"
+    return None, direct_fn, "direct calls"
+
+
+def run_c1(g, torch, dev, stream, args, flush, hbm, peak_src):
+    """ER G(n, m), n = 65,536, m = 2^20 (loops and duplicates kept), COO,
+    Union-Rem-CAS + FullShortcut without sampling, as one captured plan.  The
+    inputs fit in L2 (8 MiB), so the pass is launch- and latency-bound; the
+    fraction is reported for completeness."""
+    n, m = 65_536, 1 << 20
+    e = graphgen.er(n, m, 0x6C0A0001)
+    d_e = torch.from_numpy(e.view(np.int32)).to(dev)
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    v = g.make_variant(link="remcas", find="fullshortcut", splice="splice")
+    plan, run, how = _pass_runner(g, lambda: g.gconn_plan_create_cc(n, m, d_e, lab, v),
+                                  lambda st: g.gconn_cc(n, m, d_e, lab, v, st))
+    ts = _time_passes(torch, stream, lambda: run(stream), flush, args.warmup, max(args.steps, 5), 3000)
+    g.gconn_sync(stream)
+    if plan is not None:
+        g.gconn_plan_destroy(plan)
+    ms = float(np.mean(ts))
+    b = 8 * m + 12 * n
+    res = {"workload": "static_cc_er_n65536_m1048576", "variant": "none/remcas/fullshortcut/splice",
+           "input": "COO (uint32 pairs), resident", "launch": how, "ms": round(ms, 5),
+           "ms_median": round(float(np.median(ts)), 5), "edges_per_s": m / (ms * 1e-3),
+           "roofline": roofline(b, ms, hbm, peak_src, bytes_model="8m + 12n (COO finish + init + finalisation)",
+                                note="inputs fit in L2: launch- and latency-bound")}
+    return res, (n, e, lab.cpu().numpy().view(np.uint32).copy())
+
+
+C3_VARIANTS = [("coo", "none/remcas/naive/split_one"), ("csr", "kout/remcas/naive/split_one"),
+               ("csr", "bfs/async/naive/none"), ("coo", "none/sv/naive/none"), ("coo", "none/lt/PRF/none")]
+
+
+def run_c3(g, torch, dev, stream, args, flush, hbm, peak_src):
+    """The high-diameter workload: a 4096 x 4096 grid with 5 % of its edges
+    removed plus 64 randomly permuted paths of 2^18 vertices (n = 2^25,
+    m = 48.6 M, edge order shuffled), as COO and as CSR; one row per
+    sampling / finish variant.  Every variant's labels must equal the first
+    variant's (compared on the device); the first is compared with the
+    oracle in the CPU-baseline leg."""
+    n, e = graphgen.grid_paths(4096, 0.05, 64, 1 << 18, 0x6C0A0003)
+    m = len(e)
+    off, cols = graphgen.csr(n, e)
+    d_e = torch.from_numpy(e.view(np.int32)).to(dev)
+    d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+    d_off32 = torch.from_numpy(off.astype(np.uint32).view(np.int32)).to(dev)
+    d_cols = torch.from_numpy(cols.view(np.int32)).to(dev)
+    deg = np.diff(off.astype(np.int64))
+    first = None
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    rows = []
+    for kind, spec in C3_VARIANTS:
+        v = parse_variant(g, spec)
+        if kind == "coo":
+            plan, run, how = _pass_runner(g, lambda: g.gconn_plan_create_cc(n, m, d_e, lab, v),
+                                          lambda st: g.gconn_cc(n, m, d_e, lab, v, st))
+        else:
+            plan, run, how = _pass_runner(g, lambda: g.gconn_plan_create_cc_csr32(n, d_off32, d_cols, lab, v),
+                                          lambda st: g.gconn_cc_csr32(n, d_off32, d_cols, lab, v, st))
+        ts = _time_passes(torch, stream, lambda: run(stream), flush, 2, max(3, min(args.steps, 5)), 4000)
+        g.gconn_sync(stream)
+        if plan is not None:
+            g.gconn_plan_destroy(plan)
+        ms = float(np.mean(ts))
+        row = {"input": kind, "variant": spec, "launch": how, "ms": round(ms, 4), "edges_per_s": m / (ms * 1e-3),
+               "input_equivalent_gbs": round((8 * m + 12 * n) / (ms * 1e-3) / 1e9, 1)}
+        sample = spec.split("/")[0]
+        link = spec.split("/")[1]
+        if kind == "coo" and link not in ("sv", "lt"):
+            row["roofline"] = roofline(8 * m + 12 * n, ms, hbm, peak_src, bytes_model="8m + 12n")
+        elif kind == "coo":
+            row["roofline_lower_bound"] = roofline(8 * m + 12 * n, ms, hbm, peak_src,
+                                                   bytes_model="8m + 12n: one edge pass (the rounds re-read the "
+                                                               "edges and labels every round)")
+        else:
+            try:
+                stt = g.gconn_cc_csr_stats(n, d_off, d_cols, lab, v, stream)
+                act_v, act_a, lmax = int(stt.active_vertices), int(stt.active_arcs), int(stt.lmax)
+                if sample == "kout":
+                    samp = 4 * (n + 1) + 8 * n
+                else:   # BFS: 4 bytes per arc of the reached component
+                    hl = lab.cpu().numpy().view(np.uint32)
+                    samp = 4 * int(deg[hl == lmax].sum()) if lmax < n else 0
+                b = 4 * n + samp + 4 * n + 4 * act_a + 8 * act_v + 8 * n
+                row["roofline"] = roofline(b, ms, hbm, peak_src, active_vertices=act_v, active_arcs=act_a,
+                                           bytes_model="init 4n + sampling + VG 4n + finish + finalise 8n")
+            except g.GconnError as ex:
+                row["roofline"] = None
+                row["stats_error"] = str(ex)
+        if first is None:
+            first = lab.clone()
+            row["labels"] = "compared with the oracle (CPU-baseline leg)"
+        else:
+            row["labels_equal_first_variant"] = bool(torch.equal(lab, first))
+        rows.append(row)
+    res = {"workload": "static_cc_grid4096_paths64x2^18", "n": n, "m_undirected": m,
+           "input": "COO (uint32 pairs) and CSR (u32 offsets), resident", "l2": "flushed between passes",
+           "rows": rows}
+    out = (n, e, first.cpu().numpy().view(np.uint32).copy())
+    del d_e, d_off, d_off32, d_cols, lab, first
+    torch.cuda.empty_cache()
+    return res, out
+
+
+def run_incremental(g, torch, dev, stream, args, hbm, peak_src):
     """The insert/query stream on n = 2^24: 2^28 RMAT scale-24 insertions in
     batches of log-uniform size in [10^3, 10^8], each followed by a query
     batch of the same size of uniform random pairs.  Stream s of the
@@ -502,19 +670,23 @@ def run_incremental(g, torch, dev, stream, args):
            "batch_sizes_min_max": [min(r[0] for r in recs), max(r[0] for r in recs)],
            "latency": "device time per batch, CUDA events on the launching stream",
            "inputs": "resident in HBM"}
+    # 8 bytes per inserted pair, 9 per query (its pair and its answer byte)
+    res["roofline_insert"] = roofline(8 * nseeds * total, sum(ins_ms), hbm, peak_src, bytes_model="8 B per insert")
+    res["roofline_query"] = roofline(9 * nseeds * total, sum(q_ms), hbm, peak_src,
+                                     bytes_model="9 B per query (pair + answer byte)")
     del ins, ins0, qry, out
     torch.cuda.empty_cache()
     return res
 
 
-def run_forest(g, torch, dev, stream, args, n, M, d_off, d_cols, labels, flush):
+def run_forest(g, torch, dev, stream, args, n, M, d_off, d_cols, labels, flush, st, hbm, peak_src):
     """Spanning forest (Algorithm 2) of the same RMAT graph through
     gconn_spanning_forest_csr with device buffers; the forest must have
     n - c edges (c = components of the timed CC pass)."""
     v = parse_variant(g, args.variant)
     forest = torch.empty(n, dtype=torch.int64, device=dev)
     count = torch.zeros(1, dtype=torch.int64, device=dev)
-    plan = g.gconn_plan_create_forest_csr(n, d_off, d_cols, forest, count, None, v)
+    plan = g.gconn_plan_create_forest_csr32(n, d_off, d_cols, forest, count, None, v)
     for i in range(args.warmup):
         flush.fill_(i)
         g.gconn_plan_run(plan, stream)
@@ -533,13 +705,17 @@ def run_forest(g, torch, dev, stream, args, n, M, d_off, d_cols, labels, flush):
     comps = int(torch.unique(labels).numel())
     cnt = int(count.item())
     ms = float(np.mean(ts))
+    pass_b = sum(alg_bytes(k, st) for k in ("init", "kout", "vg", "finish")) + 4 * n + 8 * cnt
     return {"edges_per_s": M / (ms * 1e-3), "ms": round(ms, 5), "ms_median": round(float(np.median(ts)), 5),
+            "roofline": roofline(pass_b, ms, hbm, peak_src,
+                                 bytes_model="init 4n + k-out 4(n+1) + 8n + VG 4n + finish + forest slots 4n "
+                                             "+ forest ids 8(n - c)"),
             "forest_edges": cnt, "components": comps, "count_is_n_minus_c": cnt == n - comps,
             "variant": args.variant, "output": "arc positions of the forest edges (int64), compacted on device",
             "launch": "one captured plan per pass (gconn_plan_create_forest_csr)"}
 
 
-def run_batched(g, torch, dev, stream, args):
+def run_batched(g, torch, dev, stream, args, hbm, peak_src):
     """4,096 independent graphs (n log-uniform in [256, 65,536], average
     degree uniform in [4, 32], half ER half RMAT) in one captured plan,
     against one gconn_cc launch sequence per graph; both must agree exactly."""
@@ -592,6 +768,8 @@ def run_batched(g, torch, dev, stream, args):
            "edges_per_s": m_tot / (ms * 1e-3), "graphs_per_s": G / (ms * 1e-3),
            "per_graph_launches_ms": round(ms_pg, 3), "per_graph_edges_per_s": m_tot / (ms_pg * 1e-3),
            "speedup_vs_per_graph": round(ms_pg / ms, 2), "identical_labels": same,
+           "roofline": roofline(8 * m_tot + 4 * int(vo[-1]), ms, hbm, peak_src,
+                                bytes_model="8m + 4n (edges read once, labels written once)"),
            "tune": tune.as_dict(), "autotune_s": round(tune_s, 2),
            "launch": "one CUDA graph replay (a persistent kernel per size class on forked streams)"}
     del d_e, lab, lab2
@@ -739,6 +917,20 @@ def cpu_baseline(n, e, seconds):
                       f"min-id canonicalisation; median of {len(runs)} runs", "seconds": round(dt, 3),
             "runs": len(runs), "host_cores_available": os.cpu_count(), "oracle_threads": 1,
             "cpu_model": cpu_model()}
+
+
+def oracle_label_checks(legs: dict) -> dict:
+    """The labels each timed leg ended with against the oracle's (O1 on the
+    whole graph), bit for bit: part of the CPU-baseline leg, the one place
+    the benchmark runs the oracle beside the GPU path."""
+    import oracle
+    out = {}
+    for name, (n, e, lab) in legs.items():
+        t0 = time.perf_counter()
+        ref = oracle.cc_uf(n, e)
+        out[name] = bool(np.array_equal(ref, lab))
+        out[name + "_oracle_s"] = round(time.perf_counter() - t0, 2)
+    return out
 
 
 # ------------------------------------------------------------ reference arm
@@ -1008,6 +1200,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-forest", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c1", action="store_true", help="skip the ER n=65,536 COO leg")
+    ap.add_argument("--no-c3", action="store_true", help="skip the grid + paths leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-edges", type=int, default=M_EDGES)
     ap.add_argument("--clock-window", type=float, default=1.0)

@@ -158,6 +158,14 @@ gconn_status gconn_cc(uint32_t n, uint64_t m, const uint32_t* edges, uint32_t* l
 gconn_status gconn_cc_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
                           uint32_t* labels, const gconn_variant* v, void* stream);
 
+/* The same with uint32 offsets, for graphs with fewer than 2^32 arcs
+ * (Section 2's CSR with 4-byte row offsets): identical labels, half the
+ * offset bytes read by the sampling and gathering kernels.
+ *   offsets : uint32[n+1] (4-byte aligned), cols : uint32[offsets[n]]
+ * Errors as gconn_cc_csr. */
+gconn_status gconn_cc_csr32(uint32_t n, const uint32_t* offsets, const uint32_t* cols,
+                            uint32_t* labels, const gconn_variant* v, void* stream);
+
 /* ---------------------------------------------- sampling instrumentation */
 /* The quantities of Section 4.3 (Table 4 and the edges-inspected figure) for
  * one CSR run: after the sampling phase, Cov = lmax_vertices / n (vertices in
@@ -204,6 +212,10 @@ gconn_status gconn_spanning_forest(uint32_t n, uint64_t m, const uint32_t* edges
 gconn_status gconn_spanning_forest_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
                                        uint64_t* forest, uint64_t* forest_count, uint32_t* labels,
                                        const gconn_variant* v, void* stream);
+/* The same with uint32 offsets (offsets[n] < 2^32 - 1). */
+gconn_status gconn_spanning_forest_csr32(uint32_t n, const uint32_t* offsets, const uint32_t* cols,
+                                         uint64_t* forest, uint64_t* forest_count, uint32_t* labels,
+                                         const gconn_variant* v, void* stream);
 
 /* ---------------------------------------------------------- incremental */
 /* Incremental connectivity (Section 3.5, Algorithm 3).  The handle owns a
@@ -318,6 +330,12 @@ gconn_status gconn_plan_create_cc_csr(uint32_t n, const uint64_t* offsets, const
 gconn_status gconn_plan_create_forest_csr(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
                                           uint64_t* forest, uint64_t* forest_count, uint32_t* labels,
                                           const gconn_variant* v, gconn_plan** out);
+/* The plans of gconn_cc_csr32 and gconn_spanning_forest_csr32 (uint32 offsets). */
+gconn_status gconn_plan_create_cc_csr32(uint32_t n, const uint32_t* offsets, const uint32_t* cols,
+                                        uint32_t* labels, const gconn_variant* v, gconn_plan** out);
+gconn_status gconn_plan_create_forest_csr32(uint32_t n, const uint32_t* offsets, const uint32_t* cols,
+                                            uint64_t* forest, uint64_t* forest_count, uint32_t* labels,
+                                            const gconn_variant* v, gconn_plan** out);
 gconn_status gconn_plan_run(gconn_plan* p, void* stream);
 gconn_status gconn_plan_destroy(gconn_plan* p);
 
@@ -385,14 +403,19 @@ gconn_status gconn_batch_autotune(uint32_t G, const uint64_t* vtx_off, const uin
  *   labels            : device memory only, uint32[n] output
  *   v                 : sampling NONE, KOUT or HB; link ASYNC, EARLY or
  *                       REMCAS (others give GCONN_E_UNSUPPORTED)
- * Its scratch (about 16.2 MiB) is one fixed device array inside libgconn that
- * every GPU loading the library holds until the process exits.  All calls
- * share that array and it keeps the previous call's contents, so calls whose
- * GPU work overlaps (other streams, other threads) race: serialise them.  The
- * first call on each device looks the array up (cudaGetSymbolAddress, no
- * allocation); make that first call before any stream capture.  Like
- * gconn_cc_csr with device buffers, it only enqueues work: device-side errors
- * come back from gconn_sync. */
+ * Its scratch (about 16.2 MiB) is one fixed device array inside libgconn.
+ * All calls share that array and it keeps the previous call's contents, so
+ * calls whose GPU work overlaps (other streams, other threads) race:
+ * serialise them.  The first call on each device sets up: it looks the array
+ * up (cudaGetSymbolAddress) and loads the code of every kernel this call can
+ * launch.  Under lazy module loading (the CUDA default) that set-up is when
+ * the driver maps the array and the code, so it is the one call that takes
+ * device memory; from then on the GPU holds them until the process exits.  A
+ * call with n == 0 does the set-up and nothing else (its pointers are not
+ * read): make it on each device before handing the memory to another
+ * allocator, and before any stream capture.  Like gconn_cc_csr with device
+ * buffers, it only enqueues work: device-side errors come back from
+ * gconn_sync. */
 #define GCONN_NOALLOC_MAX_N 1048576u
 gconn_status gconn_cc_csr_noalloc(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
                                   uint32_t* labels, const gconn_variant* v, void* stream);

@@ -38,10 +38,20 @@ def cc(n: int, edges, variant=None, stream=None):
     return labels
 
 
+def _off32(offsets) -> bool:
+    """uint32 offsets: an int32 / uint32 tensor or array (else uint64)."""
+    dt = str(getattr(offsets, "dtype", ""))
+    return dt.endswith("int32")
+
+
 def cc_csr(n: int, offsets, cols, variant=None, stream=None):
+    """Canonical labels from CSR; int32/uint32 offsets select gconn_cc_csr32."""
     torch = _torch()
     labels = torch.empty(n, dtype=torch.int32, device=offsets.device)
-    gconn_cc_csr(n, offsets, cols, labels, variant, stream)  # noqa: F405
+    if _off32(offsets):
+        gconn_cc_csr32(n, offsets, cols, labels, variant, stream)  # noqa: F405
+    else:
+        gconn_cc_csr(n, offsets, cols, labels, variant, stream)  # noqa: F405
     return labels
 
 
@@ -64,7 +74,8 @@ def spanning_forest_csr(n: int, offsets, cols, variant=None, stream=None, labels
     forest = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
     count = torch.zeros(1, dtype=torch.int64, device=dev)
     lab = torch.empty(n, dtype=torch.int32, device=dev) if labels else None
-    gconn_spanning_forest_csr(n, offsets, cols, forest, count, lab, variant, stream)  # noqa: F405
+    fn = gconn_spanning_forest_csr32 if _off32(offsets) else gconn_spanning_forest_csr  # noqa: F405
+    fn(n, offsets, cols, forest, count, lab, variant, stream)
     c = int(count.item())
     return forest[:c], lab
 

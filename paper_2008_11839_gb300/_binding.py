@@ -123,8 +123,10 @@ _SIGS = {
     "gconn_variant_check": (_i32, [ctypes.POINTER(gconn_variant), _i32, _i32]),
     "gconn_cc": (_i32, [_u32, _u64, _vp, _vp, ctypes.POINTER(gconn_variant), _vp]),
     "gconn_cc_csr": (_i32, [_u32, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), _vp]),
+    "gconn_cc_csr32": (_i32, [_u32, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), _vp]),
     "gconn_spanning_forest": (_i32, [_u32, _u64, _vp, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), _vp]),
     "gconn_spanning_forest_csr": (_i32, [_u32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), _vp]),
+    "gconn_spanning_forest_csr32": (_i32, [_u32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), _vp]),
     "gconn_inc_create": (_i32, [_u32, ctypes.POINTER(gconn_variant), _vp, ctypes.POINTER(_vp)]),
     "gconn_inc_insert_batch": (_i32, [_vp, _u64, _vp, _vp]),
     "gconn_inc_query": (_i32, [_vp, _u64, _vp, _vp, _vp]),
@@ -144,6 +146,10 @@ _SIGS = {
     "gconn_plan_create_cc_csr": (_i32, [_u32, _vp, _vp, _vp, ctypes.POINTER(gconn_variant), ctypes.POINTER(_vp)]),
     "gconn_plan_create_forest_csr": (_i32, [_u32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(gconn_variant),
                                             ctypes.POINTER(_vp)]),
+    "gconn_plan_create_cc_csr32": (_i32, [_u32, _vp, _vp, _vp, ctypes.POINTER(gconn_variant),
+                                          ctypes.POINTER(_vp)]),
+    "gconn_plan_create_forest_csr32": (_i32, [_u32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(gconn_variant),
+                                              ctypes.POINTER(_vp)]),
     "gconn_plan_run": (_i32, [_vp, _vp]),
     "gconn_plan_destroy": (_i32, [_vp]),
     "gconn_profile_sync": (_i32, []),
@@ -272,6 +278,12 @@ def gconn_cc_csr(n, offsets, cols, labels, variant=None, stream=None):
           "gconn_cc_csr")
 
 
+def gconn_cc_csr32(n, offsets, cols, labels, variant=None, stream=None):
+    """gconn_cc_csr with uint32 offsets (fewer than 2^32 arcs)."""
+    check(lib().gconn_cc_csr32(n, ptr(offsets), ptr(cols), ptr(labels), _vref(variant), stream_handle(stream)),
+          "gconn_cc_csr32")
+
+
 def gconn_cc_csr_noalloc(n, offsets, cols, labels, variant=None, stream=None):
     """gconn_cc_csr without device allocation (device buffers, n <= 2^20)."""
     check(lib().gconn_cc_csr_noalloc(n, ptr(offsets), ptr(cols), ptr(labels), _vref(variant),
@@ -320,6 +332,11 @@ def gconn_spanning_forest_csr(n, offsets, cols, forest, forest_count, labels=Non
     check(lib().gconn_spanning_forest_csr(n, ptr(offsets), ptr(cols), ptr(forest), ptr(forest_count),
                                           ptr(labels), _vref(variant), stream_handle(stream)),
           "gconn_spanning_forest_csr")
+
+
+def gconn_spanning_forest_csr32(n, offsets, cols, forest, forest_count, labels=None, variant=None, stream=None):
+    check(lib().gconn_spanning_forest_csr32(n, ptr(offsets), ptr(cols), ptr(forest), ptr(forest_count), ptr(labels),
+                                            _vref(variant), stream_handle(stream)), "gconn_spanning_forest_csr32")
 
 
 def gconn_inc_create(n, variant=None, stream=None):
@@ -374,6 +391,21 @@ def gconn_plan_create_forest_csr(n, offsets, cols, forest, forest_count, labels=
     h = ctypes.c_void_p()
     check(lib().gconn_plan_create_forest_csr(n, ptr(offsets), ptr(cols), ptr(forest), ptr(forest_count), ptr(labels),
                                              _vref(variant), ctypes.byref(h)), "gconn_plan_create_forest_csr")
+    return h
+
+
+def gconn_plan_create_cc_csr32(n, offsets, cols, labels, variant=None):
+    h = ctypes.c_void_p()
+    check(lib().gconn_plan_create_cc_csr32(n, ptr(offsets), ptr(cols), ptr(labels), _vref(variant),
+                                           ctypes.byref(h)), "gconn_plan_create_cc_csr32")
+    return h
+
+
+def gconn_plan_create_forest_csr32(n, offsets, cols, forest, forest_count, labels=None, variant=None):
+    h = ctypes.c_void_p()
+    check(lib().gconn_plan_create_forest_csr32(n, ptr(offsets), ptr(cols), ptr(forest), ptr(forest_count),
+                                               ptr(labels), _vref(variant), ctypes.byref(h)),
+          "gconn_plan_create_forest_csr32")
     return h
 
 

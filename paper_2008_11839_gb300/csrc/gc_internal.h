@@ -35,7 +35,8 @@ constexpr uint64_t DEFAULT_SEED = 0x6C0A0001ull;
     } while (0)
 
 gconn_status cuda_status(cudaError_t e);          // maps OOM -> E_NOMEM, else E_CUDA
-uint32_t* err_word();                             // device error word of the current device
+uint32_t* err_word();                             // device error word of the current device (+ its pool)
+uint32_t* err_word_lookup();                      // the same word, without creating the scratch pool
 cudaMemPool_t scratch_pool();                     // caching scratch pool of the current device
 gconn_status read_and_clear_err(cudaStream_t st); // sync st, then read/clear the word
 
@@ -138,6 +139,32 @@ gconn_status launch_pdl(const char* name, void (*kernel)(KArgs...), dim3 grid, d
     return e == cudaSuccess ? GCONN_OK : cuda_status(e);
 }
 
+// As launch(), as a cooperative launch: every block of the grid is resident
+// at once (the grid must not exceed what the occupancy API allows), so the
+// kernel may use grid-wide barriers.
+template <class... KArgs, class... Args>
+gconn_status launch_coop(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                         cudaStream_t st, Args&&... args) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    count_capture_launch();
+    cudaGetLastError();
+    void* tok = nullptr;
+    if (g_profiling.load(std::memory_order_relaxed)) prof_begin(name, st, &tok);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    if (tok) prof_end(tok, st);
+    return e == cudaSuccess ? GCONN_OK : cuda_status(e);
+}
+
 // --------------------------------------------------------------- variant
 struct Variant {
     int sample, k, hb_n, link, find, splice, lt_rules, block;
@@ -168,6 +195,16 @@ struct IncView {
     Variant v;
 };
 bool inc_view(const gconn_inc* h, IncView* out);
+
+// The arc count of the CSR input a plan is being captured for (UINT64_MAX =
+// unknown): the plan-creation calls read offsets[n] before capturing and set
+// it for the capture, so that the parts of a pass that size a buffer from the
+// arc count need no device read (illegal while capturing).
+uint64_t csr_arcs_hint();
+struct CsrArcsHint {
+    explicit CsrArcsHint(uint64_t arcs);
+    ~CsrArcsHint();
+};
 
 // Staging of possibly-host arrays onto the device.
 gconn_status stage_in(const void* src, size_t bytes, cudaStream_t st, DevBuf& buf, const void** dev);

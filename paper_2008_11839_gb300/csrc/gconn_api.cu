@@ -67,20 +67,30 @@ cudaMemPool_t scratch_pool() {
     return g_pool[dev];
 }
 
-uint32_t* err_word() {
+static thread_local uint64_t t_csr_arcs_hint = UINT64_MAX;
+uint64_t csr_arcs_hint() { return t_csr_arcs_hint; }
+CsrArcsHint::CsrArcsHint(uint64_t arcs) { t_csr_arcs_hint = arcs; }
+CsrArcsHint::~CsrArcsHint() { t_csr_arcs_hint = UINT64_MAX; }
+
+uint32_t* err_word_lookup() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= MAX_DEV) return nullptr;
-    uint32_t* w = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_err_ptr[dev]) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_gconn_err) != cudaSuccess) return nullptr;
-            g_err_ptr[dev] = (uint32_t*)p;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_err_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_gconn_err) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
         }
-        w = g_err_ptr[dev];
+        g_err_ptr[dev] = (uint32_t*)p;
     }
+    return g_err_ptr[dev];
+}
+
+uint32_t* err_word() {
+    uint32_t* w = err_word_lookup();
+    if (!w) return nullptr;
     scratch_pool();   // created here too, so that it exists before any stream capture
     return w;
 }

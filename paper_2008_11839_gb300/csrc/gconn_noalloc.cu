@@ -20,15 +20,21 @@
 //   - all calls share the one array and it keeps the previous call's
 //     contents, so calls whose GPU work overlaps (different streams, or
 //     threads) race on it: serialise them;
-//   - the first call on each device looks the array up with
-//     cudaGetSymbolAddress (no allocation); make that first call before any
-//     stream capture.
+//   - the first call on each device (a call with n == 0 does only this)
+//     looks the array up with cudaGetSymbolAddress and loads the code of
+//     every kernel this entry point can launch.  With lazy module loading
+//     (the CUDA default) that first call is where the driver maps the array
+//     and the kernels' code, which takes device memory; later calls take
+//     none.  A caller that hands its memory to another allocator should
+//     therefore make one call (n == 0 is enough) on each device first, and
+//     before any stream capture.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <mutex>
 
 #include "gc_internal.h"
+#include "gc_static.h"
 #include "static_kernels.cuh"
 
 namespace {
@@ -53,29 +59,6 @@ constexpr size_t SCRATCH_BYTES = OFF_OVER + align256(sizeof(uint32_t) * MAX_N);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
 namespace {
-
-constexpr int MAX_DEV = 64;
-std::mutex g_setup_mu;
-unsigned char* g_scratch_dev[MAX_DEV];
-
-// Once per device, with that device current: the device address of the array.
-gconn_status scratch_ptr(unsigned char** out) {
-    int dev = 0;
-    GC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= MAX_DEV) return GCONN_E_INVAL;
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_dev[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return GCONN_E_CUDA;
-        }
-        g_scratch_dev[dev] = (unsigned char*)p;
-    }
-    *out = g_scratch_dev[dev];
-    return GCONN_OK;
-}
 
 template <class Fn>
 gconn_status dispatch_noalloc(int L, int F, int S, Fn&& fn) {
@@ -102,14 +85,83 @@ gconn_status dispatch_noalloc(int L, int F, int S, Fn&& fn) {
     return GCONN_E_UNSUPPORTED;
 }
 
+// Every (link, find, splice) triple dispatch_noalloc accepts, for loading
+// their kernels up front.
+constexpr int NA_TRIPLES[][3] = {
+    {LK_ASYNC, FD_NAIVE, SP_NONE},       {LK_ASYNC, FD_COMPRESS, SP_NONE},   {LK_ASYNC, FD_SPLIT, SP_NONE},
+    {LK_ASYNC, FD_HALVE, SP_NONE},       {LK_EARLY, FD_NAIVE, SP_NONE},      {LK_EARLY, FD_COMPRESS, SP_NONE},
+    {LK_EARLY, FD_SPLIT, SP_NONE},       {LK_EARLY, FD_HALVE, SP_NONE},      {LK_REMCAS, FD_NAIVE, SP_SPLIT_ONE},
+    {LK_REMCAS, FD_NAIVE, SP_HALVE_ONE}, {LK_REMCAS, FD_NAIVE, SP_SPLICE},   {LK_REMCAS, FD_SPLIT, SP_SPLIT_ONE},
+    {LK_REMCAS, FD_SPLIT, SP_HALVE_ONE}, {LK_REMCAS, FD_SPLIT, SP_SPLICE},   {LK_REMCAS, FD_HALVE, SP_SPLIT_ONE},
+    {LK_REMCAS, FD_HALVE, SP_HALVE_ONE}, {LK_REMCAS, FD_HALVE, SP_SPLICE},
+};
+
+template <class K>
+gconn_status load_kernel(K kernel) {
+    cudaFuncAttributes a;
+    GC_CUDA(cudaFuncGetAttributes(&a, kernel));
+    return GCONN_OK;
+}
+
+// Loads the code of every kernel gconn_cc_csr_noalloc can launch, so that no
+// later call makes the driver map code (lazy module loading would otherwise
+// do it at a kernel's first launch).
+gconn_status load_all_kernels() {
+    GC_TRY(load_kernel(k_init));
+    GC_TRY(load_kernel(k_hb1<uint64_t>));
+    GC_TRY(load_kernel(k_compress<LK_ASYNC>));
+    GC_TRY(load_kernel(k_lmax<LK_ASYNC>));
+    GC_TRY(load_kernel(k_vg<LK_ASYNC>));
+    GC_TRY(load_kernel(k_finalize));
+    for (const auto& t : NA_TRIPLES) {
+        GC_TRY(dispatch_noalloc(t[0], t[1], t[2], [&]<int l, int fr, int sp>() -> gconn_status {
+            GC_TRY(load_kernel(k_kout<l, fr, sp, false>));
+            GC_TRY(load_kernel(k_hb2<l, fr, sp, false>));
+            GC_TRY(load_kernel(k_finish_small<l, fr, sp, false>));
+            GC_TRY(load_kernel(k_finish_tasks<l, fr, sp, false>));
+            return load_kernel(k_finish_over<l, fr, sp, false>);
+        }));
+    }
+    return GCONN_OK;
+}
+
+constexpr int MAX_DEV = 64;
+std::mutex g_setup_mu;
+unsigned char* g_scratch_dev[MAX_DEV];
+
+// Once per device, with that device current: the device address of the
+// array, the device error word (looked up without creating the library's
+// memory pool) and the code of every kernel used here.
+gconn_status setup(unsigned char** out) {
+    int dev = 0;
+    GC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEV) return GCONN_E_INVAL;
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch_dev[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return GCONN_E_CUDA;
+        }
+        if (!err_word_lookup()) return GCONN_E_CUDA;
+        GC_TRY(load_all_kernels());
+        g_scratch_dev[dev] = (unsigned char*)p;
+    }
+    *out = g_scratch_dev[dev];
+    return GCONN_OK;
+}
+
 }  // namespace
 
 extern "C" gconn_status gconn_cc_csr_noalloc(uint32_t n, const uint64_t* offsets, const uint32_t* cols,
                                              uint32_t* labels, const gconn_variant* vin, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
-    if (!offsets || ((uintptr_t)offsets & 7u) || ((uintptr_t)cols & 3u)) return GCONN_E_INVAL;
     if (n > MAX_N) return GCONN_E_INVAL;
+    unsigned char* base = nullptr;
+    GC_TRY(setup(&base));   // also the whole of a call with n == 0 (any pointers)
     if (n == 0) return GCONN_OK;
+    if (!offsets || ((uintptr_t)offsets & 7u) || ((uintptr_t)cols & 3u)) return GCONN_E_INVAL;
     if (!labels || !cols) return GCONN_E_INVAL;
     // no staging copies here (they would allocate): device memory only
     if (!is_device_ptr(offsets) || !is_device_ptr(cols) || !is_device_ptr(labels)) return GCONN_E_INVAL;
@@ -118,8 +170,6 @@ extern "C" gconn_status gconn_cc_csr_noalloc(uint32_t n, const uint64_t* offsets
     if (v.sample == GCONN_SAMPLE_BFS) return GCONN_E_UNSUPPORTED;
     if (v.link != GCONN_LINK_ASYNC && v.link != GCONN_LINK_EARLY && v.link != GCONN_LINK_REMCAS)
         return GCONN_E_UNSUPPORTED;
-    unsigned char* base = nullptr;
-    GC_TRY(scratch_ptr(&base));
 
     uint32_t* hdr = (uint32_t*)(base + OFF_HEADER);
     uint32_t* lmax = hdr;
@@ -130,25 +180,11 @@ extern "C" gconn_status gconn_cc_csr_noalloc(uint32_t n, const uint64_t* offsets
     uint32_t* over = (uint32_t*)(base + OFF_OVER);
     bool sampled = v.sample != GCONN_SAMPLE_NONE;
 
-    int L = v.link;
-    int f = v.find == GCONN_FIND_FULLSHORTCUT ? GCONN_FIND_NAIVE : v.find;
-    int F = f == GCONN_FIND_COMPRESS ? FD_COMPRESS : f == GCONN_FIND_SPLIT ? FD_SPLIT
-          : f == GCONN_FIND_HALVE ? FD_HALVE : FD_NAIVE;
-    int S = SP_NONE;
-    if (L == LK_REMCAS)
-        S = v.splice == GCONN_SPLICE_SPLIT_ONE ? SP_SPLIT_ONE : v.splice == GCONN_SPLICE_HALVE_ONE ? SP_HALVE_ONE
-                                                                                                 : SP_SPLICE;
+    // the same (link, find, splice) mapping and union-find state as gconn_cc_csr
+    int L, F, S;
+    uf_triple(v, &L, &F, &S);
     int B = v.block > 0 ? v.block : 256;
-
-    UFState s;
-    s.P = labels;
-    s.H = nullptr;
-    s.W = nullptr;
-    s.sf = nullptr;
-    s.err = err_word();
-    s.n = n;
-    s.cap = v.cap;
-    s.seed = (uint32_t)(v.seed ^ (v.seed >> 32));
+    UFState s = make_state(n, labels, nullptr, nullptr, nullptr, v);
     if (!s.err) return GCONN_E_CUDA;
 
     // the counters must start at zero; everything else is written before read
@@ -160,7 +196,7 @@ extern "C" gconn_status gconn_cc_csr_noalloc(uint32_t n, const uint64_t* offsets
             GC_TRY(launch("kout", k, grid_for(k, KOUT_BLOCK, n), KOUT_BLOCK, 0, st, offsets, cols, v.k, s,
                           JobQueue{nullptr, nullptr, 0}, false));
         } else if (v.sample == GCONN_SAMPLE_HB) {
-            GC_TRY(launch("hb1", k_hb1, grid_for(k_hb1, 256, n), 256, 0, st, offsets, cols, n, s.P, s.sf, s.err));
+            GC_TRY(launch("hb1", k_hb1<uint64_t>, grid_for(k_hb1<uint64_t>, 256, n), 256, 0, st, offsets, cols, n, s.P, s.sf, s.err));
             auto k = k_hb2<l, fr, sp, false>;
             GC_TRY(launch("hb2", k, grid_for(k, B, n), B, 0, st, offsets, cols, v.hb_n, s));
         }

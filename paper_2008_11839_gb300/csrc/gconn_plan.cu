@@ -2,8 +2,8 @@
 // graph and replayed: the whole pass of Algorithm 1 (init, sampling, L_max,
 // vertex gathering, finish, finalisation) becomes one graph launch, so the
 // device runs its kernels back to back without a host launch per kernel.
-// Only variants whose pass needs no host round trip can be captured
-// (sampling none / k-out / HB, union-find finishes).
+// Every variant can be captured: BFS sampling and the round-based finishes
+// loop over their levels / rounds on the device.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,9 +57,15 @@ gconn_status capture_plan(Body&& body, gconn_plan** out) {
 
 gconn_status plan_variant_ok(const gconn_variant* vin, int input_kind, int want_forest = 0) {
     Variant v;
-    GC_TRY(resolve_variant(vin, input_kind, want_forest, &v));
-    if (v.sample == GCONN_SAMPLE_BFS || is_rounds_link(v.link))
-        return GCONN_E_UNSUPPORTED;   // these read a device flag on the host every round
+    return resolve_variant(vin, input_kind, want_forest, &v);
+}
+
+// offsets[n] of a device CSR, read before the capture starts.
+template <class OffT>
+gconn_status csr_arcs(uint32_t n, const OffT* offsets, uint64_t* out) {
+    OffT last = 0;
+    GC_CUDA(cudaMemcpy(&last, offsets + n, sizeof(OffT), cudaMemcpyDeviceToHost));
+    *out = last;
     return GCONN_OK;
 }
 
@@ -81,6 +87,9 @@ extern "C" gconn_status gconn_plan_create_cc_csr(uint32_t n, const uint64_t* off
     if (!offsets || !cols || !labels || !is_device_ptr(offsets) || !is_device_ptr(cols) || !is_device_ptr(labels))
         return GCONN_E_INVAL;
     GC_TRY(plan_variant_ok(v, 1));
+    uint64_t arcs = 0;
+    GC_TRY(csr_arcs<uint64_t>(n, offsets, &arcs));
+    CsrArcsHint hint(arcs);
     return capture_plan([&](cudaStream_t st) { return gconn_cc_csr(n, offsets, cols, labels, v, st); }, out);
 }
 
@@ -93,8 +102,41 @@ extern "C" gconn_status gconn_plan_create_forest_csr(uint32_t n, const uint64_t*
         !is_device_ptr(forest) || !is_device_ptr(forest_count) || (labels && !is_device_ptr(labels)))
         return GCONN_E_INVAL;
     GC_TRY(plan_variant_ok(v, 1, 1));
+    uint64_t arcs = 0;
+    GC_TRY(csr_arcs<uint64_t>(n, offsets, &arcs));
+    CsrArcsHint hint(arcs);
     return capture_plan([&](cudaStream_t st) {
         return gconn_spanning_forest_csr(n, offsets, cols, forest, forest_count, labels, v, st);
+    }, out);
+}
+
+extern "C" gconn_status gconn_plan_create_cc_csr32(uint32_t n, const uint32_t* offsets, const uint32_t* cols,
+                                                   uint32_t* labels, const gconn_variant* v, gconn_plan** out) {
+    if (!out) return GCONN_E_INVAL;
+    *out = nullptr;
+    if (!offsets || !cols || !labels || !is_device_ptr(offsets) || !is_device_ptr(cols) || !is_device_ptr(labels))
+        return GCONN_E_INVAL;
+    GC_TRY(plan_variant_ok(v, 1));
+    uint64_t arcs = 0;
+    GC_TRY(csr_arcs<uint32_t>(n, offsets, &arcs));
+    CsrArcsHint hint(arcs);
+    return capture_plan([&](cudaStream_t st) { return gconn_cc_csr32(n, offsets, cols, labels, v, st); }, out);
+}
+
+extern "C" gconn_status gconn_plan_create_forest_csr32(uint32_t n, const uint32_t* offsets, const uint32_t* cols,
+                                                       uint64_t* forest, uint64_t* forest_count, uint32_t* labels,
+                                                       const gconn_variant* v, gconn_plan** out) {
+    if (!out) return GCONN_E_INVAL;
+    *out = nullptr;
+    if (!offsets || !cols || !forest || !forest_count || !is_device_ptr(offsets) || !is_device_ptr(cols) ||
+        !is_device_ptr(forest) || !is_device_ptr(forest_count) || (labels && !is_device_ptr(labels)))
+        return GCONN_E_INVAL;
+    GC_TRY(plan_variant_ok(v, 1, 1));
+    uint64_t arcs = 0;
+    GC_TRY(csr_arcs<uint32_t>(n, offsets, &arcs));
+    CsrArcsHint hint(arcs);
+    return capture_plan([&](cudaStream_t st) {
+        return gconn_spanning_forest_csr32(n, offsets, cols, forest, forest_count, labels, v, st);
     }, out);
 }
 

@@ -1,12 +1,21 @@
 // gconn_rounds.cu -- round-based finish algorithms: root-based
-// Shiloach-Vishkin (Algorithm 12) and the 16 Liu-Tarjan rule sets (appendix
-// list), over a COO edge list, and the gather step that feeds them the arcs
-// of the active CSR vertices.
+// Shiloach-Vishkin (Algorithm 12), the 16 Liu-Tarjan rule sets (appendix
+// list), label propagation and Stergiou's algorithm, over a COO edge list,
+// and the gather step that feeds them the arcs of the active CSR vertices.
 //
-// Each round is a few grid-stride kernels; a device flag records whether the
-// round changed anything and the host reads it (one small copy per round).
+// Each algorithm runs as ONE cooperative launch (every block resident) that
+// loops over its rounds on the device: the phases of a round (an edge pass,
+// vertex passes) are separated by grid barriers, a round that changes
+// anything records its number in a control word, and every block reads that
+// word after the round's last barrier to decide, identically, whether to run
+// another round.  No host round trip per round, so these finishes can also be
+// captured into a CUDA graph.  Arrays that other blocks wrote earlier in the
+// same launch are read through L2 (ld.global.cg): L1 is not coherent
+// between blocks.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "gc_internal.h"
 #include "gc_static.h"
@@ -16,202 +25,291 @@ namespace gc {
 
 constexpr unsigned long long NOMSG = 0xFFFFFFFFFFFFFFFFull;
 constexpr uint32_t MAX_ROUNDS = 1u << 16;   // round cap: E_NONCONVERGED beyond it
+constexpr int RB = 256;                     // block size of the round kernels
+
+// Control words of one round kernel, zeroed before its launch.
+struct RoundCtl {
+    GridBar bar;
+    uint32_t chg;      // 1 + the last round in which something changed
+    uint32_t rounds;   // rounds run (written once, at the end)
+    uint32_t pad[4];
+};
+
+__device__ __forceinline__ uint64_t gtid() { return (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ uint64_t gstride() { return (uint64_t)gridDim.x * blockDim.x; }
+
+// Records that round r changed something (one atomic per warp); called by
+// every thread of a block at the same point.
+__device__ __forceinline__ void mark_changed(bool ch, uint32_t* chg, uint32_t r) {
+    if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicMax(chg, r + 1);
+}
+
+__device__ __forceinline__ uint64_t edge_count(uint64_t m_host, const unsigned long long* m_dev) {
+    if (!m_dev) return m_host;
+    unsigned long long m = __ldcg(m_dev);
+    return m < m_host ? m : m_host;
+}
+
+// FullShortcut while nothing links: every vertex points at its root (a walk
+// through L2), and prev (optional) receives the same value.
+__device__ __forceinline__ void compress_copy(uint32_t n, uint32_t* P, uint32_t* prev, uint32_t* err) {
+    for (uint64_t v = gtid(); v < n; v += gstride()) {
+        uint32_t p = __ldcg(P + v), r = p;
+        for (uint32_t i = 0;; ++i) {
+            uint32_t q = __ldcg(P + r);
+            if (q == r) break;
+            r = q;
+            if (i == n) { atomicOr(err, GC_DERR_NONCONV); break; }
+        }
+        if (r != p) __stcg(P + v, r);
+        if (prev) __stcg(prev + v, r);
+    }
+}
+
+// The round cap: every block reaches it in the same round.
+__device__ __forceinline__ bool over_cap(uint32_t r, uint32_t* err) {
+    if (r < MAX_ROUNDS) return false;
+    if (gtid() == 0) atomicOr(err, GC_DERR_NONCONV);
+    return true;
+}
+
+__device__ __forceinline__ void finish_rounds(RoundCtl* ctl, uint32_t r) {
+    if (gtid() == 0) ctl->rounds = r;
+}
 
 // --------------------------------------------------------------------- SV
-// Hook phase as written: labels of both endpoints are read live; the larger
-// one is writeMin'ed with the smaller when it was a root at round start.
-__global__ void __launch_bounds__(256) k_sv_hook(const uint2* __restrict__ E, uint64_t m, uint32_t n, uint32_t* P,
-                                                 const uint32_t* prev, uint32_t* changed, uint32_t* err) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    bool ch = false;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        uint2 e = E[i];
-        if (e.x >= n || e.y >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
-        uint32_t pu = __ldcg(P + e.x), pv = __ldcg(P + e.y);
-        uint32_t lo = min(pu, pv), hi = max(pu, pv);
-        if (lo != hi && prev[hi] == hi) {
-            atomicMin(P + hi, lo);
-            ch = true;
+// Shiloach-Vishkin (Algorithm 12), root-based.  Per round: the hook pass --
+// for each edge the larger of its two current labels is writeMin'ed with the
+// smaller when it was a root at round start (prev); forest form: each
+// round-start root keeps the smallest (label, edge id) message, applied in a
+// vertex pass -- then full compression, which also copies the labels into
+// prev.  Stop after a round that hooked nothing.
+template <bool SF>
+__global__ void __launch_bounds__(RB) k_sv(const uint2* __restrict__ E, const uint32_t* eids, uint64_t m_host,
+                                           const unsigned long long* m_dev, uint32_t n, uint32_t* P, uint32_t* prev,
+                                           unsigned long long* msg, uint32_t* sf, uint32_t* err, RoundCtl* ctl) {
+    const uint64_t m = edge_count(m_host, m_dev);
+    compress_copy(n, P, prev, err);
+    if (SF)
+        for (uint64_t x = gtid(); x < n; x += gstride()) msg[x] = NOMSG;
+    if (!grid_sync(&ctl->bar, err)) return;
+    for (uint32_t r = 0;; ++r) {
+        if (over_cap(r, err)) return;
+        bool ch = false;
+        for (uint64_t i = gtid(); i < m; i += gstride()) {
+            uint2 e = E[i];
+            if (e.x >= n || e.y >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
+            if (SF) {
+                uint32_t pu = __ldcg(prev + e.x), pv = __ldcg(prev + e.y);
+                if (pu == pv) continue;
+                uint32_t lo = min(pu, pv), hi = max(pu, pv);
+                uint32_t id = eids ? eids[i] : (uint32_t)i;
+                atomicMin(msg + hi, ((unsigned long long)lo << 32) | id);
+            } else {
+                uint32_t pu = __ldcg(P + e.x), pv = __ldcg(P + e.y);
+                uint32_t lo = min(pu, pv), hi = max(pu, pv);
+                if (lo != hi && __ldcg(prev + hi) == hi) {
+                    atomicMin(P + hi, lo);
+                    ch = true;
+                }
+            }
+        }
+        if (!SF) mark_changed(ch, &ctl->chg, r);
+        if (!grid_sync(&ctl->bar, err)) return;
+        if (SF) {   // apply the winning messages to round-start roots
+            for (uint64_t x = gtid(); x < n; x += gstride()) {
+                unsigned long long mv = __ldcg(msg + x);
+                if (mv == NOMSG) continue;
+                msg[x] = NOMSG;
+                uint32_t val = (uint32_t)(mv >> 32);
+                if (__ldcg(P + x) == (uint32_t)x && val < (uint32_t)x) {
+                    __stcg(P + x, val);
+                    sf[x] = (uint32_t)mv;
+                    ch = true;
+                }
+            }
+            mark_changed(ch, &ctl->chg, r);
+            if (!grid_sync(&ctl->bar, err)) return;
+        }
+        compress_copy(n, P, prev, err);
+        if (!grid_sync(&ctl->bar, err)) return;
+        if (__ldcg(&ctl->chg) != r + 1) {
+            finish_rounds(ctl, r + 1);
+            return;
         }
     }
-    if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicOr(changed, 1u);
-}
-
-// Forest variant: endpoints' round-start roots (prev) are compared, and each
-// round-start root h keeps the smallest (label, edge id) message, so the
-// recorded edge joins h's tree to the tree it is hooked under.
-__global__ void __launch_bounds__(256) k_sv_hook_sf(const uint2* __restrict__ E, const uint32_t* eids, uint64_t m,
-                                                    uint32_t n, const uint32_t* prev, unsigned long long* msg,
-                                                    uint32_t* err) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        uint2 e = E[i];
-        if (e.x >= n || e.y >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
-        uint32_t pu = prev[e.x], pv = prev[e.y];
-        if (pu == pv) continue;
-        uint32_t lo = min(pu, pv), hi = max(pu, pv);
-        uint32_t id = eids ? eids[i] : (uint32_t)i;
-        atomicMin(msg + hi, ((unsigned long long)lo << 32) | id);
-    }
-}
-
-// Apply the winning messages to roots (P[h] == h at round start) and reset.
-__global__ void k_apply_root_msgs(uint32_t n, uint32_t* P, unsigned long long* msg, uint32_t* sf,
-                                  uint32_t* changed) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    bool ch = false;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
-        unsigned long long mv = msg[x];
-        if (mv == NOMSG) continue;
-        msg[x] = NOMSG;
-        uint32_t val = (uint32_t)(mv >> 32);
-        if (P[x] == (uint32_t)x && val < (uint32_t)x) {
-            P[x] = val;
-            if (sf) sf[x] = (uint32_t)mv;
-            ch = true;
-        }
-    }
-    if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicOr(changed, 1u);
-}
-
-__global__ void k_copy_u32(uint32_t n, const uint32_t* src, uint32_t* dst) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) dst[x] = src[x];
-}
-
-__global__ void k_fill_u64(uint64_t n, unsigned long long* a, unsigned long long v) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) a[x] = v;
 }
 
 // --------------------------------------------------------------------- LT
-// Connect phase; messages are computed from the round-start parents P and
-// go to msg[] by atomicMin (packed with the edge id for forests).
+// One Liu-Tarjan rule set per launch (runtime flags).  Per round: Connect
+// messages from the round-start parents go to msg by atomicMin (packed with
+// the edge id for forests):
 //   C: u receives v, v receives u
 //   P: P[u] receives P[v], P[v] receives P[u]
 //   E: u, v, P[u], P[v] all receive min(P[u], P[v])
-__global__ void __launch_bounds__(256) k_lt_connect(const uint2* __restrict__ E, const uint32_t* eids, uint64_t m,
-                                                    uint32_t n, const uint32_t* P, int conn,
-                                                    unsigned long long* msg, uint32_t* err) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        uint2 e = E[i];
-        if (e.x == GC_DINF) continue;   // dropped by Alter
-        if (e.x >= n || e.y >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
-        if (e.x == e.y) continue;
-        unsigned long long id = eids ? eids[i] : (uint32_t)i;
-        if (conn == GCONN_LT_CONNECT) {
-            atomicMin(msg + e.x, ((unsigned long long)e.y << 32) | id);
-            atomicMin(msg + e.y, ((unsigned long long)e.x << 32) | id);
-        } else {
-            uint32_t pu = P[e.x], pv = P[e.y];
-            if (pu == pv) continue;
-            if (conn == GCONN_LT_PARENT) {
-                atomicMin(msg + pu, ((unsigned long long)pv << 32) | id);
-                atomicMin(msg + pv, ((unsigned long long)pu << 32) | id);
+// then Update (all vertices) or RootUpdate (round-start roots only), then one
+// Shortcut jump per vertex or FullShortcut, then Alter (edge <- (P[u], P[v]),
+// dropped when the ends meet).  Stop after a round that changes neither a
+// parent nor an edge; then full compression.
+__global__ void __launch_bounds__(RB) k_lt(const uint2* __restrict__ E_in, uint2* Ew, const uint32_t* eids,
+                                           uint64_t m_host, const unsigned long long* m_dev, uint32_t n, uint32_t* P,
+                                           unsigned long long* msg, uint32_t* sf, int conn, int root_only, int full,
+                                           uint32_t* err, RoundCtl* ctl) {
+    const uint64_t m = edge_count(m_host, m_dev);
+    const bool alter = Ew != nullptr;
+    for (uint64_t x = gtid(); x < n; x += gstride()) msg[x] = NOMSG;
+    if (!grid_sync(&ctl->bar, err)) return;
+    for (uint32_t r = 0;; ++r) {
+        if (over_cap(r, err)) return;
+        bool ch = false;
+        for (uint64_t i = gtid(); i < m; i += gstride()) {      // Connect
+            uint2 e = alter ? __ldcg(Ew + i) : E_in[i];
+            if (e.x == GC_DINF) continue;                       // dropped by Alter
+            if (e.x >= n || e.y >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
+            if (e.x == e.y) continue;
+            unsigned long long id = eids ? eids[i] : (uint32_t)i;
+            if (conn == GCONN_LT_CONNECT) {
+                atomicMin(msg + e.x, ((unsigned long long)e.y << 32) | id);
+                atomicMin(msg + e.y, ((unsigned long long)e.x << 32) | id);
             } else {
-                unsigned long long lo = ((unsigned long long)min(pu, pv) << 32) | id;
-                atomicMin(msg + e.x, lo);
-                atomicMin(msg + e.y, lo);
-                atomicMin(msg + pu, lo);
-                atomicMin(msg + pv, lo);
+                uint32_t pu = __ldcg(P + e.x), pv = __ldcg(P + e.y);
+                if (pu == pv) continue;
+                if (conn == GCONN_LT_PARENT) {
+                    atomicMin(msg + pu, ((unsigned long long)pv << 32) | id);
+                    atomicMin(msg + pv, ((unsigned long long)pu << 32) | id);
+                } else {
+                    unsigned long long lo = ((unsigned long long)min(pu, pv) << 32) | id;
+                    atomicMin(msg + e.x, lo);
+                    atomicMin(msg + e.y, lo);
+                    atomicMin(msg + pu, lo);
+                    atomicMin(msg + pv, lo);
+                }
             }
         }
-    }
-}
-
-// Update (all vertices) or RootUpdate (roots at round start only).
-__global__ void k_lt_update(uint32_t n, uint32_t* P, unsigned long long* msg, int root_only, uint32_t* sf,
-                            uint32_t* changed) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    bool ch = false;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
-        unsigned long long mv = msg[x];
-        if (mv == NOMSG) continue;
-        msg[x] = NOMSG;
-        uint32_t p = P[x], val = (uint32_t)(mv >> 32);
-        if (root_only && p != (uint32_t)x) continue;
-        if (val < p) {
-            P[x] = val;
-            if (sf) sf[x] = (uint32_t)mv;
-            ch = true;
+        if (!grid_sync(&ctl->bar, err)) return;
+        for (uint64_t x = gtid(); x < n; x += gstride()) {      // Update / RootUpdate
+            unsigned long long mv = __ldcg(msg + x);
+            if (mv == NOMSG) continue;
+            msg[x] = NOMSG;
+            uint32_t p = __ldcg(P + x), val = (uint32_t)(mv >> 32);
+            if (root_only && p != (uint32_t)x) continue;
+            if (val < p) {
+                __stcg(P + x, val);
+                if (sf) sf[x] = (uint32_t)mv;
+                ch = true;
+            }
+        }
+        mark_changed(ch, &ctl->chg, r);
+        if (!grid_sync(&ctl->bar, err)) return;
+        ch = false;
+        if (full) {
+            compress_copy(n, P, nullptr, err);
+        } else {                                                // one jump, in place
+            for (uint64_t x = gtid(); x < n; x += gstride()) {
+                uint32_t p = __ldcg(P + x), g2 = __ldcg(P + p);
+                if (g2 != p) {
+                    __stcg(P + x, g2);
+                    ch = true;
+                }
+            }
+            mark_changed(ch, &ctl->chg, r);
+        }
+        if (!grid_sync(&ctl->bar, err)) return;
+        if (alter) {
+            ch = false;
+            for (uint64_t i = gtid(); i < m; i += gstride()) {
+                uint2 e = __ldcg(Ew + i);
+                if (e.x == GC_DINF) continue;
+                uint2 f = make_uint2(__ldcg(P + e.x), __ldcg(P + e.y));
+                if (f.x == f.y) f = make_uint2(GC_DINF, GC_DINF);
+                if (f.x != e.x || f.y != e.y) {
+                    __stcg(Ew + i, f);
+                    ch = true;
+                }
+            }
+            mark_changed(ch, &ctl->chg, r);
+            if (!grid_sync(&ctl->bar, err)) return;
+        }
+        if (__ldcg(&ctl->chg) != r + 1) {
+            finish_rounds(ctl, r + 1);
+            break;
         }
     }
-    if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicOr(changed, 1u);
-}
-
-// Shortcut: one pointer jump per vertex (in place).
-__global__ void k_lt_shortcut(uint32_t n, uint32_t* P, uint32_t* changed) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    bool ch = false;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
-        uint32_t p = __ldcg(P + x), g = __ldcg(P + p);
-        if (g != p) {
-            __stcg(P + x, g);
-            ch = true;
-        }
-    }
-    if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicOr(changed, 1u);
-}
-
-// Alter: every edge becomes (P[u], P[v]); an edge whose ends meet is dropped.
-__global__ void k_lt_alter(uint2* E, uint64_t m, const uint32_t* P, uint32_t* changed) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    bool ch = false;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        uint2 e = E[i];
-        if (e.x == GC_DINF) continue;
-        uint2 f = make_uint2(P[e.x], P[e.y]);
-        if (f.x == f.y) f = make_uint2(GC_DINF, GC_DINF);
-        if (f.x != e.x || f.y != e.y) {
-            E[i] = f;
-            ch = true;
-        }
-    }
-    if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicOr(changed, 1u);
+    compress_copy(n, P, nullptr, err);
 }
 
 // --------------------------------------------------------------------- LP
-// Label Propagation round: the larger label of each edge takes the smaller.
-__global__ void __launch_bounds__(256) k_lp(const uint2* __restrict__ E, uint64_t m, uint32_t n, uint32_t* P,
-                                            uint32_t* changed, uint32_t* err) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    bool ch = false;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        uint2 e = E[i];
-        if (e.x >= n || e.y >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
-        uint32_t a = __ldcg(P + e.x), b = __ldcg(P + e.y);
-        if (a == b) continue;
-        uint32_t lo = min(a, b);
-        if (a > lo) atomicMin(P + e.x, lo);
-        if (b > lo) atomicMin(P + e.y, lo);
-        ch = true;
+// Label Propagation: per round, for each edge the larger endpoint label takes
+// the smaller (atomicMin on both ends); stop after a round that changes
+// nothing; then full compression.
+__global__ void __launch_bounds__(RB) k_lp(const uint2* __restrict__ E, uint64_t m_host,
+                                           const unsigned long long* m_dev, uint32_t n, uint32_t* P, uint32_t* err,
+                                           RoundCtl* ctl) {
+    const uint64_t m = edge_count(m_host, m_dev);
+    for (uint32_t r = 0; m; ++r) {
+        if (over_cap(r, err)) return;
+        bool ch = false;
+        for (uint64_t i = gtid(); i < m; i += gstride()) {
+            uint2 e = E[i];
+            if (e.x >= n || e.y >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
+            uint32_t a = __ldcg(P + e.x), b = __ldcg(P + e.y);
+            if (a == b) continue;
+            uint32_t lo = min(a, b);
+            if (a > lo) atomicMin(P + e.x, lo);
+            if (b > lo) atomicMin(P + e.y, lo);
+            ch = true;
+        }
+        mark_changed(ch, &ctl->chg, r);
+        if (!grid_sync(&ctl->bar, err)) return;
+        if (__ldcg(&ctl->chg) != r + 1) {
+            finish_rounds(ctl, r + 1);
+            break;
+        }
     }
-    if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicOr(changed, 1u);
+    compress_copy(n, P, nullptr, err);
 }
 
 // ---------------------------------------------------------------- Stergiou
-// One round over the previous labels: the entry of each endpoint's label
-// receives the other endpoint's label (atomicMin into the current array).
-__global__ void __launch_bounds__(256) k_stergiou(const uint2* __restrict__ E, uint64_t m, uint32_t n,
-                                                  const uint32_t* prev, uint32_t* P, uint32_t* err) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        uint2 e = E[i];
-        if (e.x >= n || e.y >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
-        uint32_t a = prev[e.x], b = prev[e.y];
-        if (a == b) continue;
-        if (b < a) atomicMin(P + a, b);
-        else atomicMin(P + b, a);
+// Per round: for each edge the entry of the larger of prev[u], prev[v]
+// receives the smaller (atomicMin into the current labels), then one
+// shortcut jump per vertex; the round changed something if a jump moved or a
+// label differs from prev.  The shortcut pass also writes the next round's
+// prev (each entry is written there by its own thread only).
+__global__ void __launch_bounds__(RB) k_stergiou(const uint2* __restrict__ E, uint64_t m_host,
+                                                 const unsigned long long* m_dev, uint32_t n, uint32_t* P,
+                                                 uint32_t* prev, uint32_t* err, RoundCtl* ctl) {
+    const uint64_t m = edge_count(m_host, m_dev);
+    for (uint64_t x = gtid(); x < n; x += gstride()) prev[x] = __ldcg(P + x);
+    if (!grid_sync(&ctl->bar, err)) return;
+    for (uint32_t r = 0; m; ++r) {
+        if (over_cap(r, err)) return;
+        for (uint64_t i = gtid(); i < m; i += gstride()) {
+            uint2 e = E[i];
+            if (e.x >= n || e.y >= n) { atomicOr(err, GC_DERR_RANGE); continue; }
+            uint32_t a = __ldcg(prev + e.x), b = __ldcg(prev + e.y);
+            if (a == b) continue;
+            if (b < a) atomicMin(P + a, b);
+            else atomicMin(P + b, a);
+        }
+        if (!grid_sync(&ctl->bar, err)) return;
+        bool ch = false;
+        for (uint64_t x = gtid(); x < n; x += gstride()) {
+            uint32_t p = __ldcg(P + x), g2 = __ldcg(P + p);
+            if (g2 != p) {
+                __stcg(P + x, g2);
+                ch = true;
+            }
+            if (__ldcg(prev + x) != g2) ch = true;
+            __stcg(prev + x, g2);
+        }
+        mark_changed(ch, &ctl->chg, r);
+        if (!grid_sync(&ctl->bar, err)) return;
+        if (__ldcg(&ctl->chg) != r + 1) {
+            finish_rounds(ctl, r + 1);
+            break;
+        }
     }
-}
-
-// Compare the current labels with the previous ones (a change means another round).
-__global__ void k_changed(uint32_t n, const uint32_t* prev, const uint32_t* P, uint32_t* changed) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    bool ch = false;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) ch |= prev[x] != P[x];
-    if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicOr(changed, 1u);
+    compress_copy(n, P, nullptr, err);
 }
 
 // ------------------------------------------------------------- CSR gather
@@ -230,7 +328,8 @@ __device__ __forceinline__ void gather_arc(const Gather& g, uint32_t u, uint32_t
     }
 }
 
-__global__ void k_gather_small(const uint64_t* off, const uint32_t* cols, uint32_t n, const uint32_t* active,
+template <class OffT>
+__global__ void k_gather_small(const OffT* off, const uint32_t* cols, uint32_t n, const uint32_t* active,
                                const uint32_t* small, const uint32_t* nsmall, Gather g, uint32_t* err) {
     uint32_t cnt = *nsmall;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -244,7 +343,8 @@ __global__ void k_gather_small(const uint64_t* off, const uint32_t* cols, uint32
     }
 }
 
-__global__ void k_gather_tasks(const uint64_t* off, const uint32_t* cols, uint32_t n, const uint32_t* active,
+template <class OffT>
+__global__ void k_gather_tasks(const OffT* off, const uint32_t* cols, uint32_t n, const uint32_t* active,
                                const unsigned long long* tasks, const uint32_t* ntasks, uint32_t task_cap, Gather g,
                                uint32_t* err) {
     uint32_t cnt = min(*ntasks, task_cap);
@@ -263,7 +363,8 @@ __global__ void k_gather_tasks(const uint64_t* off, const uint32_t* cols, uint32
     }
 }
 
-__global__ void k_gather_over(const uint64_t* off, const uint32_t* cols, uint32_t n, const uint32_t* active,
+template <class OffT>
+__global__ void k_gather_over(const OffT* off, const uint32_t* cols, uint32_t n, const uint32_t* active,
                               const uint32_t* over, const uint32_t* nover, Gather g, uint32_t* err) {
     uint64_t cnt = *nover;
     for (uint64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
@@ -277,73 +378,52 @@ __global__ void k_gather_over(const uint64_t* off, const uint32_t* cols, uint32_
 }
 
 // ------------------------------------------------------------------ drivers
-struct RoundFlag {
-    DevBuf dev;
-    uint32_t* host = nullptr;
+// Scratch for one round kernel: its control words (zeroed on the stream).
+struct RoundLaunch {
+    DevBuf ctlb;
+    RoundCtl* ctl = nullptr;
     gconn_status init(cudaStream_t st) {
-        GC_TRY(dev.alloc(sizeof(uint32_t), st));
-        if (cudaMallocHost(&host, sizeof(uint32_t)) != cudaSuccess) return GCONN_E_NOMEM;
+        GC_TRY(ctlb.alloc(sizeof(RoundCtl), st));
+        ctl = ctlb.as<RoundCtl>();
+        GC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(RoundCtl), st));
         return GCONN_OK;
     }
-    ~RoundFlag() {
-        if (host) cudaFreeHost(host);
-    }
-    uint32_t* d() { return dev.as<uint32_t>(); }
-    gconn_status reset(cudaStream_t st) {
-        GC_CUDA(cudaMemsetAsync(d(), 0, sizeof(uint32_t), st));
-        return GCONN_OK;
-    }
-    gconn_status read(cudaStream_t st, bool* out) {
-        GC_CUDA(cudaMemcpyAsync(host, d(), sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    // Rounds run, for the edge-pass count (waits for the stream).
+    gconn_status rounds(cudaStream_t st, uint32_t* out) {
+        uint32_t r = 0;
+        GC_CUDA(cudaMemcpyAsync(&r, &ctl->rounds, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         GC_CUDA(cudaStreamSynchronize(st));
-        *out = *host != 0;
+        *out = r;
         return GCONN_OK;
     }
 };
 
-static gconn_status run_sv(const Variant& v, const UFState& s, const uint2* E, const uint32_t* eids, uint64_t m,
-                           cudaStream_t st, uint32_t& passes) {
+template <class K>
+unsigned round_grid(K kernel, uint64_t m, uint32_t n) {
+    return grid_for(kernel, RB, std::max<uint64_t>(m, n));
+}
+
+static gconn_status run_sv(const UFState& s, const uint2* E, const uint32_t* eids, uint64_t m,
+                           const unsigned long long* m_dev, cudaStream_t st, uint32_t* rounds) {
     uint32_t n = s.n;
     DevBuf prevb, msgb;
     GC_TRY(prevb.alloc(sizeof(uint32_t) * (size_t)n, st));
-    uint32_t* prev = prevb.as<uint32_t>();
     unsigned long long* msg = nullptr;
     bool sf = s.sf != nullptr;
-    unsigned gn = grid_for(k_copy_u32, 256, n);
     if (sf) {
         GC_TRY(msgb.alloc(sizeof(unsigned long long) * (size_t)n, st));
         msg = msgb.as<unsigned long long>();
-        GC_TRY(launch("fill_u64", k_fill_u64, grid_for(k_fill_u64, 256, n), 256, 0, st, (uint64_t)n, msg, NOMSG));
     }
-    RoundFlag flag;
-    GC_TRY(flag.init(st));
-    Variant va = v;
-    va.link = GCONN_LINK_ASYNC;
-    GC_TRY(compress_all(va, s, st));
-    GC_TRY(launch("sv_copy", k_copy_u32, gn, 256, 0, st, n, (const uint32_t*)s.P, prev));
-    for (uint32_t round = 0;; ++round) {
-        if (round >= MAX_ROUNDS) return GCONN_E_NONCONVERGED;
-        GC_TRY(flag.reset(st));
-        ++passes;
-        if (sf) {
-            GC_TRY(launch("sv_hook_sf", k_sv_hook_sf, grid_for(k_sv_hook_sf, 256, m), 256, 0, st, E, eids, m, n,
-                          (const uint32_t*)prev, msg, s.err));
-            GC_TRY(launch("sv_apply", k_apply_root_msgs, gn, 256, 0, st, n, s.P, msg, s.sf, flag.d()));
-        } else {
-            GC_TRY(launch("sv_hook", k_sv_hook, grid_for(k_sv_hook, 256, m), 256, 0, st, E, m, n, s.P,
-                          (const uint32_t*)prev, flag.d(), s.err));
-        }
-        GC_TRY(compress_all(va, s, st));
-        GC_TRY(launch("sv_copy", k_copy_u32, gn, 256, 0, st, n, (const uint32_t*)s.P, prev));
-        bool changed = false;
-        GC_TRY(flag.read(st, &changed));
-        if (!changed) break;
-    }
-    return GCONN_OK;
+    RoundLaunch rl;
+    GC_TRY(rl.init(st));
+    auto k = sf ? k_sv<true> : k_sv<false>;
+    GC_TRY(launch_coop("sv", k, round_grid(k, m, n), RB, 0, st, E, eids, m, m_dev, n, s.P, prevb.as<uint32_t>(), msg,
+                       s.sf, s.err, rl.ctl));
+    return rounds ? rl.rounds(st, rounds) : GCONN_OK;
 }
 
 static gconn_status run_lt(const Variant& v, const UFState& s, const uint2* E_in, const uint32_t* eids, uint64_t m,
-                           cudaStream_t st, uint32_t& passes) {
+                           const unsigned long long* m_dev, cudaStream_t st, uint32_t* rounds) {
     uint32_t n = s.n;
     int conn = v.lt_rules & 3;
     bool root_only = (v.lt_rules & GCONN_LT_ROOTUPDATE) != 0;
@@ -351,111 +431,71 @@ static gconn_status run_lt(const Variant& v, const UFState& s, const uint2* E_in
     bool alter = (v.lt_rules & GCONN_LT_ALTER) != 0;
     DevBuf msgb, eb;
     GC_TRY(msgb.alloc(sizeof(unsigned long long) * (size_t)n, st));
-    unsigned long long* msg = msgb.as<unsigned long long>();
-    GC_TRY(launch("fill_u64", k_fill_u64, grid_for(k_fill_u64, 256, n), 256, 0, st, (uint64_t)n, msg, NOMSG));
-    const uint2* E = E_in;
     uint2* Ew = nullptr;
-    if (alter && m) {
+    if (alter && m) {   // Alter rewrites the edges: work on a copy
         GC_TRY(eb.alloc(sizeof(uint2) * m, st));
         Ew = eb.as<uint2>();
         GC_CUDA(cudaMemcpyAsync(Ew, E_in, sizeof(uint2) * m, cudaMemcpyDeviceToDevice, st));
-        E = Ew;
     }
-    RoundFlag flag;
-    GC_TRY(flag.init(st));
-    Variant va = v;
-    va.link = GCONN_LINK_ASYNC;
-    unsigned gn = grid_for(k_lt_update, 256, n);
-    for (uint32_t round = 0;; ++round) {
-        if (round >= MAX_ROUNDS) return GCONN_E_NONCONVERGED;
-        GC_TRY(flag.reset(st));
-        passes += (m ? 1u : 0u) + (alter && m ? 1u : 0u);   // connect (+ alter) read every edge
-        if (m)
-            GC_TRY(launch("lt_connect", k_lt_connect, grid_for(k_lt_connect, 256, m), 256, 0, st, E, eids, m, n,
-                          (const uint32_t*)s.P, conn, msg, s.err));
-        GC_TRY(launch("lt_update", k_lt_update, gn, 256, 0, st, n, s.P, msg, (int)root_only, s.sf, flag.d()));
-        if (full) {
-            GC_TRY(compress_all(va, s, st));
-        } else {
-            GC_TRY(launch("lt_shortcut", k_lt_shortcut, gn, 256, 0, st, n, s.P, flag.d()));
-        }
-        if (alter && m)
-            GC_TRY(launch("lt_alter", k_lt_alter, grid_for(k_lt_alter, 256, m), 256, 0, st, Ew, m,
-                          (const uint32_t*)s.P, flag.d()));
-        bool changed = false;
-        GC_TRY(flag.read(st, &changed));
-        if (!changed) break;
-    }
-    return compress_all(va, s, st);
+    RoundLaunch rl;
+    GC_TRY(rl.init(st));
+    GC_TRY(launch_coop("lt", k_lt, round_grid(k_lt, m, n), RB, 0, st, E_in, Ew, eids, m, m_dev, n, s.P,
+                       msgb.as<unsigned long long>(), s.sf, conn, (int)root_only, (int)full, s.err, rl.ctl));
+    if (!rounds) return GCONN_OK;
+    GC_TRY(rl.rounds(st, rounds));
+    *rounds *= (m ? 1u : 0u) + (alter && m ? 1u : 0u);   // connect (+ alter) read every edge
+    return GCONN_OK;
 }
 
-static gconn_status run_lp(const Variant& v, const UFState& s, const uint2* E, uint64_t m, cudaStream_t st,
-                           uint32_t& passes) {
-    RoundFlag flag;
-    GC_TRY(flag.init(st));
-    for (uint32_t round = 0; m; ++round) {
-        if (round >= MAX_ROUNDS) return GCONN_E_NONCONVERGED;
-        GC_TRY(flag.reset(st));
-        ++passes;
-        GC_TRY(launch("lp", k_lp, grid_for(k_lp, 256, m), 256, 0, st, E, m, s.n, s.P, flag.d(), s.err));
-        bool changed = false;
-        GC_TRY(flag.read(st, &changed));
-        if (!changed) break;
-    }
-    Variant va = v;
-    va.link = GCONN_LINK_ASYNC;
-    return compress_all(va, s, st);
+static gconn_status run_lp(const UFState& s, const uint2* E, uint64_t m, const unsigned long long* m_dev,
+                           cudaStream_t st, uint32_t* rounds) {
+    RoundLaunch rl;
+    GC_TRY(rl.init(st));
+    GC_TRY(launch_coop("lp", k_lp, round_grid(k_lp, m, s.n), RB, 0, st, E, m, m_dev, s.n, s.P, s.err, rl.ctl));
+    return rounds ? rl.rounds(st, rounds) : GCONN_OK;
 }
 
-static gconn_status run_stergiou(const Variant& v, const UFState& s, const uint2* E, uint64_t m, cudaStream_t st,
-                                 uint32_t& passes) {
-    uint32_t n = s.n;
+static gconn_status run_stergiou(const UFState& s, const uint2* E, uint64_t m, const unsigned long long* m_dev,
+                                 cudaStream_t st, uint32_t* rounds) {
     DevBuf prevb;
-    GC_TRY(prevb.alloc(sizeof(uint32_t) * (size_t)n, st));
-    uint32_t* prev = prevb.as<uint32_t>();
-    RoundFlag flag;
-    GC_TRY(flag.init(st));
-    unsigned gn = grid_for(k_copy_u32, 256, n);
-    for (uint32_t round = 0; m; ++round) {
-        if (round >= MAX_ROUNDS) return GCONN_E_NONCONVERGED;
-        GC_TRY(flag.reset(st));
-        GC_TRY(launch("stergiou_copy", k_copy_u32, gn, 256, 0, st, n, (const uint32_t*)s.P, prev));
-        ++passes;
-        GC_TRY(launch("stergiou", k_stergiou, grid_for(k_stergiou, 256, m), 256, 0, st, E, m, n,
-                      (const uint32_t*)prev, s.P, s.err));
-        GC_TRY(launch("lt_shortcut", k_lt_shortcut, gn, 256, 0, st, n, s.P, flag.d()));
-        GC_TRY(launch("stergiou_changed", k_changed, gn, 256, 0, st, n, (const uint32_t*)prev,
-                      (const uint32_t*)s.P, flag.d()));
-        bool changed = false;
-        GC_TRY(flag.read(st, &changed));
-        if (!changed) break;
-    }
-    Variant va = v;
-    va.link = GCONN_LINK_ASYNC;
-    return compress_all(va, s, st);
+    GC_TRY(prevb.alloc(sizeof(uint32_t) * (size_t)s.n, st));
+    RoundLaunch rl;
+    GC_TRY(rl.init(st));
+    GC_TRY(launch_coop("stergiou", k_stergiou, round_grid(k_stergiou, m, s.n), RB, 0, st, E, m, m_dev, s.n, s.P,
+                       prevb.as<uint32_t>(), s.err, rl.ctl));
+    return rounds ? rl.rounds(st, rounds) : GCONN_OK;
 }
 
 gconn_status rounds_coo(const Variant& v, const UFState& s, const uint32_t* edges, const uint32_t* eids, uint64_t m,
-                        cudaStream_t st, uint32_t* edge_passes) {
+                        cudaStream_t st, uint32_t* edge_passes, const unsigned long long* m_dev) {
     uint32_t passes = 0;
+    uint32_t* pp = edge_passes ? &passes : nullptr;
     gconn_status r = GCONN_OK;
+    const uint2* E = (const uint2*)edges;
     if (s.n == 0) r = GCONN_OK;
-    else if (v.link == GCONN_LINK_SV) r = run_sv(v, s, (const uint2*)edges, eids, m, st, passes);
-    else if (v.link == GCONN_LINK_LP) r = run_lp(v, s, (const uint2*)edges, m, st, passes);
-    else if (v.link == GCONN_LINK_STERGIOU) r = run_stergiou(v, s, (const uint2*)edges, m, st, passes);
-    else r = run_lt(v, s, (const uint2*)edges, eids, m, st, passes);
+    else if (v.link == GCONN_LINK_SV) r = run_sv(s, E, eids, m, m_dev, st, pp);
+    else if (v.link == GCONN_LINK_LP) r = run_lp(s, E, m, m_dev, st, pp);
+    else if (v.link == GCONN_LINK_STERGIOU) r = run_stergiou(s, E, m, m_dev, st, pp);
+    else r = run_lt(v, s, E, eids, m, m_dev, st, pp);
     if (edge_passes) *edge_passes = passes;
     return r;
 }
 
-gconn_status rounds_csr(const Variant& v, const UFState& s, const uint64_t* off, const uint32_t* cols,
+template <class OffT>
+gconn_status rounds_csr(const Variant& v, const UFState& s, const OffT* off, const uint32_t* cols,
                         const uint32_t* active, const uint32_t* small, const uint32_t* nsmall,
                         const unsigned long long* tasks, const uint32_t* ntasks, uint32_t task_cap,
                         const uint32_t* over, const uint32_t* nover, cudaStream_t st) {
     uint32_t n = s.n;
-    uint64_t narcs = 0;
-    GC_CUDA(cudaMemcpyAsync(&narcs, off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    GC_CUDA(cudaStreamSynchronize(st));
+    // the gathered arcs are at most all arcs: the host needs offsets[n] to
+    // size the list (known in advance while a plan is being captured)
+    uint64_t narcs = csr_arcs_hint();
+    if (narcs == UINT64_MAX) {
+        OffT last = 0;
+        GC_CUDA(cudaMemcpyAsync(&last, off + n, sizeof(OffT), cudaMemcpyDeviceToHost, st));
+        GC_CUDA(cudaStreamSynchronize(st));
+        narcs = last;
+    }
     DevBuf eb, ib, cb;
     uint64_t cap = narcs ? narcs : 1;
     GC_TRY(eb.alloc(sizeof(uint2) * cap, st));
@@ -463,17 +503,23 @@ gconn_status rounds_csr(const Variant& v, const UFState& s, const uint64_t* off,
     GC_TRY(cb.alloc(sizeof(unsigned long long), st));
     Gather g{eb.as<uint2>(), ib.as<uint32_t>(), cb.as<unsigned long long>(), cap};
     GC_CUDA(cudaMemsetAsync(g.cnt, 0, sizeof(unsigned long long), st));
-    GC_TRY(launch("gather_small", k_gather_small, grid_for(k_gather_small, 256, n), 256, 0, st, off, cols, n, active,
-                  small, nsmall, g, s.err));
-    GC_TRY(launch("gather_tasks", k_gather_tasks, grid_for(k_gather_tasks, 256, (uint64_t)n * 32), 256, 0, st, off,
-                  cols, n, active, tasks, ntasks, task_cap, g, s.err));
-    GC_TRY(launch("gather_over", k_gather_over, grid_for(k_gather_over, 256, (uint64_t)n * 256), 256, 0, st, off,
-                  cols, n, active, over, nover, g, s.err));
-    unsigned long long m = 0;
-    GC_CUDA(cudaMemcpyAsync(&m, g.cnt, sizeof(m), cudaMemcpyDeviceToHost, st));
-    GC_CUDA(cudaStreamSynchronize(st));
-    if (m > cap) m = cap;
-    return rounds_coo(v, s, (const uint32_t*)g.E, g.ids, m, st);
+    GC_TRY(launch("gather_small", k_gather_small<OffT>, grid_for(k_gather_small<OffT>, 256, n), 256, 0, st, off,
+                  cols, n, active, small, nsmall, g, s.err));
+    GC_TRY(launch("gather_tasks", k_gather_tasks<OffT>, grid_for(k_gather_tasks<OffT>, 256, (uint64_t)n * 32), 256,
+                  0, st, off, cols, n, active, tasks, ntasks, task_cap, g, s.err));
+    GC_TRY(launch("gather_over", k_gather_over<OffT>, grid_for(k_gather_over<OffT>, 256, (uint64_t)n * 256), 256, 0,
+                  st, off, cols, n, active, over, nover, g, s.err));
+    // the rounds read the gathered count on the device
+    return rounds_coo(v, s, (const uint32_t*)g.E, g.ids, cap, st, nullptr, g.cnt);
 }
+
+template gconn_status rounds_csr<uint32_t>(const Variant&, const UFState&, const uint32_t*, const uint32_t*,
+                                          const uint32_t*, const uint32_t*, const uint32_t*,
+                                          const unsigned long long*, const uint32_t*, uint32_t, const uint32_t*,
+                                          const uint32_t*, cudaStream_t);
+template gconn_status rounds_csr<uint64_t>(const Variant&, const UFState&, const uint64_t*, const uint32_t*,
+                                          const uint32_t*, const uint32_t*, const uint32_t*,
+                                          const unsigned long long*, const uint32_t*, uint32_t, const uint32_t*,
+                                          const uint32_t*, cudaStream_t);
 
 }  // namespace gc

@@ -137,10 +137,10 @@ __device__ __forceinline__ void union_or_defer(const UFState& s, const JobQueue&
     uf_union<L, F, S, SF>(s, a, b, eid, sp);
 }
 
-template <int L, int F, int S, bool SF>
+template <int L, int F, int S, bool SF, class OffT = uint64_t>
 // plain: one thread per vertex over its first k arcs (the form without the
 // per-warp packing; also taken for k > KOUT_WARP_K).
-static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const uint64_t* __restrict__ off,
+static __global__ void __launch_bounds__(KOUT_BLOCK) k_kout(const OffT* __restrict__ off,
                                                             const uint32_t* __restrict__ cols, int k, UFState s,
                                                             JobQueue dq, bool plain) {
     pdl_entry();
@@ -302,20 +302,43 @@ static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_
 // union done: no block waits for another, the last one just does more work.
 // It reads parents through L2 only, since its own L1 may hold lines from
 // before other blocks' links.
+// With mode_out set instead, block 0 computes the most frequent root label
+// of the samples right away, while the other blocks run the deferred unions
+// (grids of at least two blocks): a label's root only moves down its own
+// set, so the fused tail kernel takes L_max = root(mode) once every union is
+// done -- the same choice of set without serialising 1,024 walks behind the
+// unions.
 template <int L, int F, int S, bool SF>
 static __global__ void __launch_bounds__(LMAX_SAMPLES) k_union_jobs(UFState s, JobQueue dq, uint64_t seed,
-                                                           uint32_t* lmax_out, uint32_t* done) {
+                                                           uint32_t* lmax_out, uint32_t* done, uint32_t* mode_out) {
     pdl_entry();
+    __shared__ LmaxSmem sm;
     unsigned long long cnt = *dq.count;
     if (cnt > dq.cap) cnt = dq.cap;
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
+    uint64_t b0 = blockIdx.x, nb = gridDim.x;
+    if (mode_out && nb > 1) {
+        if (blockIdx.x == 0) {
+            block_lmax<L == LK_JTB ? LK_JTB : LK_ASYNC, false>(s, seed, mode_out, sm);
+            return;
+        }
+        b0 -= 1;
+        nb -= 1;
+    }
+    uint64_t stride = nb * blockDim.x;
+    for (uint64_t i = b0 * blockDim.x + threadIdx.x; i < cnt; i += stride) {
         KoutJob jb = dq.jobs[i];
         Spin sp(s.cap);
         uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
     }
+    if (mode_out) {                    // a one-block grid: the mode after the unions
+        if (nb == gridDim.x) {
+            __syncthreads();
+            __threadfence();
+            block_lmax<L == LK_JTB ? LK_JTB : LK_ASYNC, false>(s, seed, mode_out, sm);
+        }
+        return;
+    }
     if (!lmax_out) return;
-    __shared__ LmaxSmem sm;
     __shared__ bool last;
     __threadfence();
     __syncthreads();
@@ -328,7 +351,8 @@ static __global__ void __launch_bounds__(LMAX_SAMPLES) k_union_jobs(UFState s, J
 
 // HB sampling step 1 (Algorithm 3): P[v] = min(v, w) for the smallest
 // neighbour w = cols[off[v]].  Each thread writes only its own P[v].
-static __global__ void k_hb1(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols, uint32_t n,
+template <class OffT = uint64_t>
+static __global__ void k_hb1(const OffT* __restrict__ off, const uint32_t* __restrict__ cols, uint32_t n,
                       uint32_t* P, uint32_t* sf, uint32_t* err) {
     pdl_entry();
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -350,7 +374,8 @@ static __global__ void k_hb1(const uint64_t* __restrict__ off, const uint32_t* _
 // records arc off[v]; hooks are cleared and so is `zero` (the pass's
 // counters).  Every thread writes only its own entries and nothing reads P in
 // this kernel, so step 1 needs no separate initialisation pass before it.
-static __global__ void k_hb_init(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols, uint32_t n,
+template <class OffT = uint64_t>
+static __global__ void k_hb_init(const OffT* __restrict__ off, const uint32_t* __restrict__ cols, uint32_t n,
                                  uint32_t* P, uint32_t* H, uint32_t* sf, uint32_t* err, uint32_t* zero,
                                  uint32_t nzero) {
     pdl_entry();
@@ -383,8 +408,8 @@ static __global__ void k_hb_init(const uint64_t* __restrict__ off, const uint32_
 // would leave most lanes idle while a few run four unions in sequence.
 constexpr int HB_WARP_N = 4;
 
-template <int L, int F, int S, bool SF>
-static __global__ void __launch_bounds__(256) k_hb2w(const uint64_t* __restrict__ off,
+template <int L, int F, int S, bool SF, class OffT = uint64_t>
+static __global__ void __launch_bounds__(256) k_hb2w(const OffT* __restrict__ off,
                                                      const uint32_t* __restrict__ cols, int N, UFState s,
                                                      JobQueue dq) {
     pdl_entry();
@@ -445,8 +470,8 @@ static __global__ void __launch_bounds__(256) k_hb2w(const uint64_t* __restrict_
 // HB sampling step 2: every vertex that is still a root after step 1 unions
 // its first N edges.  "Still a root after step 1" is read from the row (no
 // smaller neighbour), not from P, which step-2 unions change concurrently.
-template <int L, int F, int S, bool SF>
-static __global__ void __launch_bounds__(256) k_hb2(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols,
+template <int L, int F, int S, bool SF, class OffT = uint64_t>
+static __global__ void __launch_bounds__(256) k_hb2(const OffT* __restrict__ off, const uint32_t* __restrict__ cols,
                                              int N, UFState s) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < s.n; v += stride) {
@@ -498,8 +523,8 @@ static __global__ void k_w_from_p(uint32_t n, const uint32_t* P, u64w* W) {
 // tasks.  A vertex whose tasks do not fit the task array goes to the overflow
 // list (one block per vertex).  With `active` non-null one bit per vertex
 // records the active set for the arc filter of the finish kernels.
-template <int L, bool COMPRESS = false>
-static __global__ void __launch_bounds__(256) k_vg(const uint64_t* __restrict__ off, UFState s, const uint32_t* lmax_p,
+template <int L, bool COMPRESS = false, class OffT = uint64_t>
+static __global__ void __launch_bounds__(256) k_vg(const OffT* __restrict__ off, UFState s, const uint32_t* lmax_p,
                                             uint32_t* active, uint32_t* small, uint32_t* nsmall,
                                             unsigned long long* tasks, uint32_t task_cap, uint32_t* ntasks,
                                             uint32_t* over, uint32_t* nover) {
@@ -551,21 +576,28 @@ static __global__ void __launch_bounds__(256) k_vg(const uint64_t* __restrict__ 
     }
 }
 
-// Vertex gathering with full compression for the min-linking rules, written
-// for few instructions per vertex: a warp takes 128 consecutive vertices, each
-// lane 4 of them, with one 16-byte parent load and two 16-byte offset loads
-// (the fifth offset is the next lane's first).  The lane's 4 root walks run in
-// lock step, changed parents go back in one 16-byte store, and the 4 active
-// bits of each lane are merged into the bitmask words by three shuffles.  The
-// list appends (rare after sampling) run only in warps that have active
-// vertices.  Needs 16-byte aligned offsets and parents; others use k_vg.
-template <int L>
-static __global__ void __launch_bounds__(256) k_vg4(const uint64_t* __restrict__ off, UFState s,
-                                                    const uint32_t* lmax_p, uint32_t* active, uint32_t* small,
-                                                    uint32_t* nsmall, unsigned long long* tasks, uint32_t task_cap,
-                                                    uint32_t* ntasks, uint32_t* over, uint32_t* nover) {
-    pdl_entry();
-    const uint32_t lmax = lmax_p ? *lmax_p : GC_DINF;
+// Four consecutive CSR offsets from one 16-byte aligned address.
+template <class OffT>
+__device__ __forceinline__ void load_off4(const OffT* p, uint64_t o[4]) {
+    if constexpr (sizeof(OffT) == 4) {
+        uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    } else {
+        ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
+        ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(p) + 1);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+}
+
+// The body of k_vg4 over this grid's share of the 128-vertex groups (also
+// a phase of the fused tail kernel).  Parent loads may use L1 (L1P): no
+// union runs while it does, so a stale line holds an older ancestor and the
+// walks still end at the current roots.
+template <int L, class OffT, bool L1P>
+__device__ __forceinline__ void vg4_pass(const OffT* __restrict__ off, const UFState& s, uint32_t lmax,
+                                         uint32_t* active, uint32_t* small, uint32_t* nsmall,
+                                         unsigned long long* tasks, uint32_t task_cap, uint32_t* ntasks,
+                                         uint32_t* over, uint32_t* nover) {
     const uint64_t n = s.n;
     const uint64_t nwords = (n + 31) / 32;
     const uint64_t ngroups = (n + 127) / 128;
@@ -577,27 +609,26 @@ static __global__ void __launch_bounds__(256) k_vg4(const uint64_t* __restrict__
         uint32_t p[4];
         uint64_t o[5];
         if (full) {
-            uint4 pp = __ldca(reinterpret_cast<const uint4*>(s.P + v0));
-            ulonglong2 a = *reinterpret_cast<const ulonglong2*>(off + v0);
-            ulonglong2 b = *reinterpret_cast<const ulonglong2*>(off + v0 + 2);
+            uint4 pp = L1P ? __ldca(reinterpret_cast<const uint4*>(s.P + v0))
+                           : __ldcg(reinterpret_cast<const uint4*>(s.P + v0));
+            load_off4(off + v0, o);
             p[0] = pp.x; p[1] = pp.y; p[2] = pp.z; p[3] = pp.w;
-            o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 bool in = v0 + j < n;
-                p[j] = in ? ldq<true>(s.P, (uint32_t)(v0 + j)) : 0u;   // vertex 0 is its own root
-                o[j] = v0 + j <= n ? off[v0 + j] : 0;                   // off[n] ends the last row
+                p[j] = in ? ldq<L1P>(s.P, (uint32_t)(v0 + j)) : 0u;   // vertex 0 is its own root
+                o[j] = v0 + j <= n ? (uint64_t)off[v0 + j] : 0;       // off[n] ends the last row
             }
         }
         uint64_t nx = __shfl_down_sync(0xFFFFFFFFu, o[0], 1);   // next lane's off[v0 + 4]
-        if (lane == 31 || v0 + 4 >= n) nx = v0 + 4 <= n ? off[v0 + 4] : 0;
+        if (lane == 31 || v0 + 4 >= n) nx = v0 + 4 <= n ? (uint64_t)off[v0 + 4] : 0;
         o[4] = nx;
         uint32_t cur[4], nxt[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             cur[j] = p[j];
-            nxt[j] = cur[j] < s.n ? ldq<true>(s.P, cur[j]) : cur[j];
+            nxt[j] = cur[j] < s.n ? ldq<L1P>(s.P, cur[j]) : cur[j];
         }
         for (uint32_t step = 0; step <= s.n; ++step) {
             bool any = false;
@@ -610,7 +641,7 @@ static __global__ void __launch_bounds__(256) k_vg4(const uint64_t* __restrict__
             }
             if (!any) break;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) nxt[j] = cur[j] < s.n ? ldq<true>(s.P, cur[j]) : cur[j];
+            for (int j = 0; j < 4; ++j) nxt[j] = cur[j] < s.n ? ldq<L1P>(s.P, cur[j]) : cur[j];
             if (step == s.n) atomicOr(s.err, GC_DERR_NONCONV);
         }
         // P[v] = root(v)
@@ -670,16 +701,39 @@ static __global__ void __launch_bounds__(256) k_vg4(const uint64_t* __restrict__
     }
 }
 
+// Vertex gathering with full compression for the min-linking rules, written
+// for few instructions per vertex: a warp takes 128 consecutive vertices, each
+// lane 4 of them, with one 16-byte parent load and 16 bytes (uint32 offsets)
+// or 32 bytes (uint64) of offsets (the fifth offset is the next lane's first).
+// The lane's 4 root walks run in lock step, changed parents go back in one
+// 16-byte store, and the 4 active bits of each lane are merged into the
+// bitmask words by three shuffles.  The list appends (rare after sampling)
+// run only in warps that have active vertices.  Needs 16-byte aligned offsets
+// and parents; others use k_vg.
+template <int L, class OffT = uint64_t>
+static __global__ void __launch_bounds__(256) k_vg4(const OffT* __restrict__ off, UFState s,
+                                                    const uint32_t* lmax_p, uint32_t* active, uint32_t* small,
+                                                    uint32_t* nsmall, unsigned long long* tasks, uint32_t task_cap,
+                                                    uint32_t* ntasks, uint32_t* over, uint32_t* nover) {
+    pdl_entry();
+    const uint32_t lmax = lmax_p ? *lmax_p : GC_DINF;
+    vg4_pass<L, OffT, true>(off, s, lmax, active, small, nsmall, tasks, task_cap, ntasks, over, nover);
+}
+
+// COH: the bitmask was written by other blocks of the same kernel, so it is
+// read through L2 instead of the read-only path.
+template <bool COH = false>
 __device__ __forceinline__ bool arc_needed(const uint32_t* active, uint32_t u, uint32_t v) {
     // each undirected edge is processed once: from its larger endpoint when
     // both are active, from the active one when the other was skipped
     if (v < u) return true;
     if (!active) return false;
-    return ((__ldg(active + (v >> 5)) >> (v & 31)) & 1u) == 0;
+    uint32_t w = COH ? __ldcg(active + (v >> 5)) : __ldg(active + (v >> 5));
+    return ((w >> (v & 31)) & 1u) == 0;
 }
 
-template <int L, int F, int S, bool SF>
-static __global__ void __launch_bounds__(256) k_finish_small(const uint64_t* __restrict__ off,
+template <int L, int F, int S, bool SF, class OffT = uint64_t>
+static __global__ void __launch_bounds__(256) k_finish_small(const OffT* __restrict__ off,
                                                       const uint32_t* __restrict__ cols, UFState s,
                                                       const uint32_t* active, const uint32_t* small,
                                                       const uint32_t* nsmall) {
@@ -700,8 +754,8 @@ static __global__ void __launch_bounds__(256) k_finish_small(const uint64_t* __r
     }
 }
 
-template <int L, int F, int S, bool SF>
-static __global__ void __launch_bounds__(256) k_finish_tasks(const uint64_t* __restrict__ off,
+template <int L, int F, int S, bool SF, class OffT = uint64_t>
+static __global__ void __launch_bounds__(256) k_finish_tasks(const OffT* __restrict__ off,
                                                       const uint32_t* __restrict__ cols, UFState s,
                                                       const uint32_t* active, const unsigned long long* tasks,
                                                       const uint32_t* ntasks, uint32_t task_cap) {
@@ -725,31 +779,29 @@ static __global__ void __launch_bounds__(256) k_finish_tasks(const uint64_t* __r
     }
 }
 
-// The whole finish phase in one launch: 256-arc warp tasks first, then the
+// The whole finish phase over this grid: 256-arc warp tasks first, then the
 // low-degree list (thread per vertex), then overflow vertices (warp per
-// vertex striding over all its arcs).
-template <int L, int F, int S, bool SF>
-__global__ void __launch_bounds__(256) k_finish(const uint64_t* __restrict__ off, const uint32_t* __restrict__ cols,
-                                               UFState s, const uint32_t* active, const uint32_t* small,
-                                               const uint32_t* nsmall, const unsigned long long* tasks,
-                                               const uint32_t* ntasks, uint32_t task_cap, const uint32_t* over,
-                                               const uint32_t* nover) {
-    pdl_entry();
-    uint32_t ct = *ntasks;
-    if (ct > task_cap) ct = task_cap;
+// vertex striding over all its arcs).  ct / cs / co are the task, low-degree
+// and overflow counts; COH reads the lists and the bitmask through L2 (they
+// were written earlier in the same kernel by other blocks).
+template <int L, int F, int S, bool SF, class OffT, bool COH>
+__device__ __forceinline__ void finish_pass(const OffT* __restrict__ off, const uint32_t* __restrict__ cols,
+                                            const UFState& s, const uint32_t* active, const uint32_t* small,
+                                            uint32_t cs, const unsigned long long* tasks, uint32_t ct,
+                                            const uint32_t* over, uint32_t co) {
     uint64_t nw = (uint64_t)gridDim.x * (blockDim.x / 32);
     uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     unsigned lane = lane_id();
     for (uint64_t t = gw; t < ct; t += nw) {
         if (err_abort(s.err)) return;
-        unsigned long long task = tasks[t];
+        unsigned long long task = COH ? __ldcg(tasks + t) : tasks[t];
         uint32_t u = (uint32_t)(task >> 32);
-        uint64_t lo = off[u] + (task & 0xFFFFFFFFull) * TASK_ARCS, hi = off[u + 1];
+        uint64_t lo = (uint64_t)off[u] + (task & 0xFFFFFFFFull) * TASK_ARCS, hi = off[u + 1];
         if (lo + TASK_ARCS < hi) hi = lo + TASK_ARCS;
         for (uint64_t a = lo + lane; a < hi; a += 32) {
             uint32_t v = cols[a];
             if (v >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
-            if (!arc_needed(active, u, v)) continue;
+            if (!arc_needed<COH>(active, u, v)) continue;
             Spin sp(s.cap);
             uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
         }
@@ -760,7 +812,6 @@ __global__ void __launch_bounds__(256) k_finish(const uint64_t* __restrict__ off
     // list: a short list (the usual case after sampling) is spread one vertex
     // per warp, so no warp walks several rows' unions in sequence; a long one
     // packs up to 32 vertices per warp.
-    uint32_t cs = *nsmall;
     uint64_t G = ((uint64_t)cs + nw - 1) / nw;
     G = G < 1 ? 1 : G > 32 ? 32 : G;
     for (uint64_t base = gw * G; base < cs; base += nw * G) {
@@ -769,7 +820,7 @@ __global__ void __launch_bounds__(256) k_finish(const uint64_t* __restrict__ off
         uint32_t u = 0, d = 0;
         uint64_t lo = 0;
         if (lane < G && i < cs) {
-            u = small[i];
+            u = COH ? __ldcg(small + i) : small[i];
             lo = off[u];
             d = (uint32_t)(off[u + 1] - lo);
         }
@@ -797,22 +848,33 @@ __global__ void __launch_bounds__(256) k_finish(const uint64_t* __restrict__ off
             uint64_t a = olo + (j - oex);
             uint32_t v = cols[a];
             if (v >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
-            if (!arc_needed(active, ou, v)) continue;
+            if (!arc_needed<COH>(active, ou, v)) continue;
             Spin sp(s.cap);
             uf_union<L, F, S, SF>(s, ou, v, (uint32_t)a, sp);
         }
     }
-    uint32_t co = *nover;
     for (uint64_t i = gw; i < co; i += nw) {
-        uint32_t u = over[i];
-        for (uint64_t a = off[u] + lane; a < off[u + 1]; a += 32) {
+        uint32_t u = COH ? __ldcg(over + i) : over[i];
+        for (uint64_t a = (uint64_t)off[u] + lane; a < off[u + 1]; a += 32) {
             uint32_t v = cols[a];
             if (v >= s.n) { atomicOr(s.err, GC_DERR_RANGE); continue; }
-            if (!arc_needed(active, u, v)) continue;
+            if (!arc_needed<COH>(active, u, v)) continue;
             Spin sp(s.cap);
             uf_union<L, F, S, SF>(s, u, v, (uint32_t)a, sp);
         }
     }
+}
+
+template <int L, int F, int S, bool SF, class OffT = uint64_t>
+__global__ void __launch_bounds__(256) k_finish(const OffT* __restrict__ off, const uint32_t* __restrict__ cols,
+                                               UFState s, const uint32_t* active, const uint32_t* small,
+                                               const uint32_t* nsmall, const unsigned long long* tasks,
+                                               const uint32_t* ntasks, uint32_t task_cap, const uint32_t* over,
+                                               const uint32_t* nover) {
+    pdl_entry();
+    uint32_t ct = *ntasks;
+    if (ct > task_cap) ct = task_cap;
+    finish_pass<L, F, S, SF, OffT, false>(off, cols, s, active, small, *nsmall, tasks, ct, over, *nover);
 }
 
 // Finish without vertex gathering (measurement form, GCONN_ABL_NO_VG): one
@@ -822,8 +884,8 @@ __global__ void __launch_bounds__(256) k_finish(const uint64_t* __restrict__ off
 // Skipping stays exact: a vertex seen with parent L_max is in L_max's tree,
 // membership never ends, so an edge skipped from both ends joins two vertices
 // already connected.
-template <int L, int F, int S, bool SF>
-static __global__ void __launch_bounds__(256) k_finish_plain(const uint64_t* __restrict__ off,
+template <int L, int F, int S, bool SF, class OffT = uint64_t>
+static __global__ void __launch_bounds__(256) k_finish_plain(const OffT* __restrict__ off,
                                                              const uint32_t* __restrict__ cols, UFState s,
                                                              const uint32_t* lmax_p) {
     pdl_entry();
@@ -842,8 +904,8 @@ static __global__ void __launch_bounds__(256) k_finish_plain(const uint64_t* __r
 }
 
 // Overflow vertices: one block strides over all arcs of one vertex.
-template <int L, int F, int S, bool SF>
-static __global__ void __launch_bounds__(256) k_finish_over(const uint64_t* __restrict__ off,
+template <int L, int F, int S, bool SF, class OffT = uint64_t>
+static __global__ void __launch_bounds__(256) k_finish_over(const OffT* __restrict__ off,
                                                      const uint32_t* __restrict__ cols, UFState s,
                                                      const uint32_t* active, const uint32_t* over,
                                                      const uint32_t* nover) {
@@ -866,6 +928,7 @@ static __global__ void __launch_bounds__(256) k_finish_over(const uint64_t* __re
 // with one 16-byte load; the four walks advance in lock step (four parent loads in
 // flight), and the four labels are written back only when one changed (after
 // the vertex-gathering pass most vertices already point at their root).
+template <bool L1 = true>
 __device__ __forceinline__ void finalize_all(const UFState& s, uint32_t* labels) {
     constexpr int W = 4;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -876,7 +939,7 @@ __device__ __forceinline__ void finalize_all(const UFState& s, uint32_t* labels)
         uint4 p4 = __ldcg(reinterpret_cast<const uint4*>(s.P) + q);
         uint32_t cur[W] = {p4.x, p4.y, p4.z, p4.w}, nxt[W];
 #pragma unroll
-        for (int j = 0; j < W; ++j) nxt[j] = ldq<true>(s.P, cur[j]);
+        for (int j = 0; j < W; ++j) nxt[j] = ldq<L1>(s.P, cur[j]);
         for (uint32_t step = 0; step <= s.n; ++step) {
             bool any = false;
 #pragma unroll
@@ -888,13 +951,13 @@ __device__ __forceinline__ void finalize_all(const UFState& s, uint32_t* labels)
             }
             if (!any) break;
 #pragma unroll
-            for (int j = 0; j < W; ++j) nxt[j] = ldq<true>(s.P, cur[j]);
+            for (int j = 0; j < W; ++j) nxt[j] = ldq<L1>(s.P, cur[j]);
             if (step == s.n) atomicOr(s.err, GC_DERR_NONCONV);
         }
         if (cur[0] != p4.x || cur[1] != p4.y || cur[2] != p4.z || cur[3] != p4.w)
             reinterpret_cast<uint4*>(labels)[q] = make_uint4(cur[0], cur[1], cur[2], cur[3]);
     }
-    for (uint64_t v = nv * 4 + t0; v < s.n; v += stride) labels[v] = uf_root<LK_ASYNC, true>(s, (uint32_t)v);
+    for (uint64_t v = nv * 4 + t0; v < s.n; v += stride) labels[v] = uf_root<LK_ASYNC, L1>(s, (uint32_t)v);
 }
 
 static __global__ void k_finalize(UFState s, uint32_t* labels) {
@@ -908,26 +971,131 @@ static __global__ void k_finalize(UFState s, uint32_t* labels) {
 // have edges and a label other than L_max, so all of them are in the gathered
 // lists) or the L_max root itself.  So while P[L_max] is still L_max, walking
 // the listed vertices to their roots finalises every label; otherwise (or
-// without an L_max) every vertex is walked.
+// without an L_max) every vertex is walked.  L1: parent loads may use L1
+// (not when this grid's own earlier phase linked roots).
+template <bool L1>
+__device__ __forceinline__ void finalize_gathered_pass(const UFState& s, uint32_t lmax, const uint32_t* small,
+                                                       uint64_t cs, const unsigned long long* tasks, uint64_t ct,
+                                                       const uint32_t* over, uint64_t co) {
+    if (lmax >= s.n || ldp(s.P, lmax) != lmax) {
+        finalize_all<L1>(s, s.P);
+        return;
+    }
+    uint64_t total = cs + ct + co;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        uint32_t u = i < cs ? __ldcg(small + i) : i < cs + ct ? (uint32_t)(__ldcg(tasks + (i - cs)) >> 32)
+                                                              : __ldcg(over + (i - cs - ct));
+        uint32_t r = uf_root<LK_ASYNC, L1>(s, u);
+        if (ldp(s.P, u) != r) stp(s.P, u, r);
+    }
+}
+
 static __global__ void k_finalize_gathered(UFState s, const uint32_t* lmax_p, const uint32_t* small,
                                            const uint32_t* nsmall, const unsigned long long* tasks,
                                            const uint32_t* ntasks, uint32_t task_cap, const uint32_t* over,
                                            const uint32_t* nover) {
     pdl_entry();
     uint32_t lmax = lmax_p ? *lmax_p : GC_DINF;
-    if (lmax >= s.n || ldp(s.P, lmax) != lmax) {
-        finalize_all(s, s.P);
-        return;
-    }
-    uint64_t cs = *nsmall, ct = *ntasks, co = *nover;
+    uint64_t ct = *ntasks;
     if (ct > task_cap) ct = task_cap;
-    uint64_t total = cs + ct + co;
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        uint32_t u = i < cs ? small[i] : i < cs + ct ? (uint32_t)(tasks[i - cs] >> 32) : over[i - cs - ct];
-        uint32_t r = uf_root<LK_ASYNC, true>(s, u);
-        if (ldp(s.P, u) != r) stp(s.P, u, r);
+    finalize_gathered_pass<true>(s, lmax, small, *nsmall, tasks, ct, over, *nover);
+}
+
+// ------------------------------------------------------------ grid barrier
+// A barrier over every block of a cooperative launch (all blocks resident).
+// Two words, zero-initialised: arrivals and a generation.  Thread 0 of each
+// block reads the generation, then arrives; the last arrival resets the count
+// and advances the generation; the others wait for it to change.  The wait is
+// bounded: it ends when the device error word shows that a block gave up, or
+// after GRID_WAIT_NS, when it raises that error itself -- then every block
+// returns instead of waiting forever.
+struct GridBar {
+    uint32_t count, gen;
+};
+constexpr unsigned long long GRID_WAIT_NS = 20ull * 1000000000ull;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+static __device__ __noinline__ bool grid_sync(GridBar* b, uint32_t* err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        uint32_t g = ld_acquire_gpu(&b->gen);
+        __threadfence();                     // this block's writes before its arrival
+        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+            atomicExch(&b->count, 0u);
+            st_release_gpu(&b->gen, g + 1);
+        } else {
+            unsigned long long t0 = globaltimer_ns();
+            unsigned ns = 32;
+            while (ld_acquire_gpu(&b->gen) == g) {
+                if (__ldcg(err) & GC_DERR_NONCONV) { good = 0; break; }
+                if (globaltimer_ns() - t0 > GRID_WAIT_NS) {
+                    atomicOr(err, GC_DERR_NONCONV);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns *= 2;
+            }
+        }
+        __threadfence();
+        ok = good;
     }
+    __syncthreads();
+    return ok != 0;
+}
+
+// The CSR pass after sampling in one cooperative launch (every block
+// resident), phases separated by grid barriers: L_max = root(mode) (each
+// block walks it; the sampled mode label, or BFS's L_max, or none), then
+// vertex gathering with full compression (vg4_pass), barrier, the
+// load-balanced finish (finish_pass), barrier, and finalisation from the
+// gathered lists (finalize_gathered_pass).  The phases are those of
+// k_vg4 / k_finish / k_finalize_gathered; one launch instead of three saves
+// two grid launches and drains on a pass whose finish touches only the
+// ~10^3 vertices sampling left active.  Lists, counters and the bitmask are
+// read through L2 after a barrier (other blocks wrote them), and the
+// finalisation walks through L2 (the finish linked roots in other blocks).
+// hdr: [0] L_max (written here), [1..3] gathering counters, [12..13] the grid
+// barrier -- all zeroed by the init kernel.
+constexpr int TAIL_BLOCK = 256;
+
+template <int L, int F, int S, bool SF, class OffT>
+static __global__ void __launch_bounds__(TAIL_BLOCK) k_tail(const OffT* __restrict__ off,
+                                                            const uint32_t* __restrict__ cols, UFState s,
+                                                            uint32_t* hdr, const uint32_t* mode_p, uint32_t* active,
+                                                            uint32_t* small, unsigned long long* tasks,
+                                                            uint32_t task_cap, uint32_t* over, int finalize) {
+    GridBar* bar = reinterpret_cast<GridBar*>(hdr + 12);
+    __shared__ uint32_t s_lmax;
+    if (threadIdx.x == 0) s_lmax = mode_p ? uf_root<LK_ASYNC, false>(s, __ldcg(mode_p)) : GC_DINF;
+    __syncthreads();
+    const uint32_t lmax = s_lmax;
+    if (mode_p && blockIdx.x == 0 && threadIdx.x == 0) hdr[0] = lmax;
+    vg4_pass<L, OffT, true>(off, s, lmax, active, small, hdr + 1, tasks, task_cap, hdr + 2, over, hdr + 3);
+    if (!grid_sync(bar, s.err)) return;
+    const uint32_t cs = __ldcg(hdr + 1), co = __ldcg(hdr + 3);
+    uint32_t ct = __ldcg(hdr + 2);
+    if (ct > task_cap) ct = task_cap;
+    finish_pass<L, F, S, SF, OffT, true>(off, cols, s, active, small, cs, tasks, ct, over, co);
+    if (!finalize) return;
+    if (!grid_sync(bar, s.err)) return;
+    finalize_gathered_pass<false>(s, lmax, small, cs, tasks, ct, over, co);
 }
 
 // Union-JTB roots are not minimal: canonicalise through the root.
@@ -995,8 +1163,9 @@ static __global__ void __launch_bounds__(256) k_sf_compact(uint32_t n, const uin
 }
 
 // offsets[n] must fit a 32-bit forest id.
-static __global__ void k_check_arcs(const uint64_t* off, uint32_t n, uint32_t* err) {
-    if (off[n] >= 0xFFFFFFFFull) atomicOr(err, GC_DERR_OVERFLOW);
+template <class OffT = uint64_t>
+static __global__ void k_check_arcs(const OffT* off, uint32_t n, uint32_t* err) {
+    if ((uint64_t)off[n] >= 0xFFFFFFFFull) atomicOr(err, GC_DERR_OVERFLOW);
 }
 
 }  // namespace gc

@@ -19,13 +19,24 @@ def _lib():
     g.build()
 
 
+def _variant(spec):
+    s, l, f, sp = spec.split("/")
+    if l == "lt":
+        return g.make_variant(sample=s, link=l, lt=f)
+    return g.make_variant(sample=s, link=l, find=f, splice=sp)
+
+
+# BFS sampling and the round-based finishes loop on the device, so they are
+# captured like the rest
 @pytest.mark.parametrize("spec", ["kout/remcas/naive/split_one", "hb/async/compress/none", "none/early/naive/none",
-                                  "kout/jtb/twotrysplit/none", "kout/hooks/halve/none"])
+                                  "kout/jtb/twotrysplit/none", "kout/hooks/halve/none",
+                                  "bfs/remcas/naive/split_one", "bfs/async/naive/none", "bfs/jtb/naive/none",
+                                  "kout/sv/naive/none", "none/sv/naive/none", "hb/lt/PRF/none", "none/lt/CUSA/none",
+                                  "kout/lp/naive/none", "none/stergiou/naive/none"])
 def test_csr_plan_replay_and_refill(spec):
     import torch
     n = 30_011
-    s, l, f, sp = spec.split("/")
-    v = g.make_variant(sample=s, link=l, find=f, splice=sp)
+    v = _variant(spec)
     e1 = graphgen.rmat(15, 90_000, 1) % np.uint32(n)
     e2 = graphgen.er(n, 90_000, 2)
     off1, cols1 = graphgen.csr(n, e1)
@@ -46,7 +57,7 @@ def test_csr_plan_replay_and_refill(spec):
     g.gconn_plan_destroy(p)
 
 
-def test_coo_plan_and_unsupported():
+def test_coo_plans_incl_round_finishes():
     import torch
     n = 5000
     e = graphgen.er(n, 7000, 3)
@@ -56,10 +67,17 @@ def test_coo_plan_and_unsupported():
     g.gconn_sync()
     assert (host_u32(lab) == oracle.cc_uf(n, e)).all()
     g.gconn_plan_destroy(p)
-    for kw in (dict(link="sv"), dict(link="lt", lt="PRF")):
-        with pytest.raises(g.GconnError) as ex:
-            g.gconn_plan_create_cc(n, len(e), dev(e), lab, g.make_variant(**kw))
-        assert ex.value.status == g.GCONN_E_UNSUPPORTED
+    de = dev(e)
+    ref = oracle.cc_uf(n, e)
+    for kw in (dict(link="sv"), dict(link="lt", lt="PRF"), dict(link="lt", lt="EUSA"), dict(link="lp"),
+               dict(link="stergiou")):
+        p = g.gconn_plan_create_cc(n, len(e), de, lab, g.make_variant(**kw))
+        for _ in range(2):
+            lab.fill_(-1)
+            g.gconn_plan_run(p)
+            g.gconn_sync()
+            assert (host_u32(lab) == ref).all(), kw
+        g.gconn_plan_destroy(p)
     with pytest.raises(g.GconnError):
         g.gconn_plan_create_cc(n, len(e), e, lab)        # host edges cannot be captured
 
@@ -110,19 +128,18 @@ def test_profile_select_times_only_named_kernels():
     g.gconn_profile_reset()
 
 
-@pytest.mark.parametrize("spec", ["kout/remcas/naive/split_one", "hb/early/naive/none", "none/async/halve/none"])
+@pytest.mark.parametrize("spec", ["kout/remcas/naive/split_one", "hb/early/naive/none", "none/async/halve/none",
+                                  "bfs/remcas/naive/split_one", "none/sv/naive/none", "kout/lt/PRS/none"])
 def test_forest_plan_replays_valid_forests(spec):
     import torch
     n = 25_013
     e = graphgen.rmat(15, 70_000, 9) % np.uint32(n)
     off, cols = graphgen.csr(n, e)
     ref = oracle.cc_uf(n, e)
-    s, l, f, sp = spec.split("/")
     forest = torch.empty(n, dtype=torch.int64, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     lab = torch.empty(n, dtype=torch.int32, device="cuda")
-    p = g.gconn_plan_create_forest_csr(n, dev(off), dev(cols), forest, cnt, lab,
-                                       g.make_variant(sample=s, link=l, find=f, splice=sp))
+    p = g.gconn_plan_create_forest_csr(n, dev(off), dev(cols), forest, cnt, lab, _variant(spec))
     for _ in range(2):
         g.gconn_plan_run(p)
         g.gconn_sync()
