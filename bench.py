@@ -135,17 +135,17 @@ def make_static_input(rank: int, scale: int = SCALE, m: int = M_EDGES):
     return n, e, off, cols, seed
 
 
-def inc_batches(seed: int):
-    """Insert-batch sizes floor(10^(3+5U)) until 2^28 (last one truncated)."""
+def inc_batches(seed: int, total: int = INC_TOTAL):
+    """Insert-batch sizes floor(10^(3+5U)) until `total` (last one truncated)."""
     h = graphgen.hash_fill(seed, 11, 0, 4096)
     sizes, tot = [], 0
     for x in h:
         u = (int(x) >> 11) * 2.0 ** -53
         b = int(10 ** (3 + 5 * u))
-        b = min(b, INC_TOTAL - tot)
+        b = min(b, total - tot)
         sizes.append(b)
         tot += b
-        if tot >= INC_TOTAL:
+        if tot >= total:
             break
     return sizes
 
@@ -777,84 +777,156 @@ def run_batched(g, torch, dev, stream, args, hbm, peak_src):
     return res
 
 
+def rmat_stream(scale, total, seed, perm, threads=16):
+    """Edges [0, total) of the seeded RMAT stream, generated in parallel
+    chunks (the C generator releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    out = np.empty((total, 2), np.uint32)
+    chunk = -(-total // threads)
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda s0: graphgen.rmat_range(scale, s0, min(chunk, total - s0), seed, perm=perm,
+                                                   out=out[s0:s0 + min(chunk, total - s0)]),
+                    range(0, total, chunk)))
+    return out
+
+
+def serving_trace(sessions, n_scale, total, seed):
+    """Per session s: its own RMAT scale-24 insert stream (seed + s) and as
+    many uniform query pairs, cut into insert batches of log-uniform size in
+    [10^3, 10^8] (the incremental workload's law), each followed by a query
+    batch of the same size; requests are (op, pairs) in session order."""
+    n = 1 << n_scale
+    perm = graphgen.permutation(n, seed, 6)
+    out = []
+    for s in range(sessions):
+        ins = rmat_stream(n_scale, total, seed + s, perm)
+        qry = graphgen.pairs_range(n, 0, total, seed + s)
+        reqs, a = [], 0
+        for b in inc_batches(seed + s, total):
+            reqs.append((0, ins[a:a + b]))
+            reqs.append((1, qry[a:a + b]))
+            a += b
+        out.append(reqs)
+    return n, out
+
+
 def run_serving(g, torch, args):
-    """8 sessions (n = 2^20 each), 64 requests per session alternating insert
-    and query batches of log-uniform size in [10^3, 10^5] (host buffers).
-    Plain form: one synchronous gconn_inc_* call per request in round-robin
-    order.  Served form: every session submits all its requests at once from
-    its own thread to one gconn_server.  Answers must be identical."""
-    import threading
-    S, R, n, scale = 8, 64, 1 << 20, 20
-    rng = np.random.default_rng(SEED_SERVE)
-    perm = graphgen.permutation(n, SEED_SERVE, 6)
-    streams = []
-    for s in range(S):
-        reqs, ip, qp = [], 0, 0
-        for r in range(R):
-            c = int(10 ** rng.uniform(3, 5))
-            if r % 2 == 0:
-                e = graphgen.rmat_range(scale, (s << 32) + ip, c, SEED_SERVE, perm=perm)
-                ip += c
-                reqs.append((g.GCONN_OP_INSERT, e))
-            else:
-                reqs.append((g.GCONN_OP_QUERY, graphgen.pairs_range(n, (s << 32) + qp, c, SEED_SERVE)))
-                qp += c
-        streams.append(reqs)
-    total_ops = sum(len(a) for reqs in streams for _, a in reqs)
+    """Continuous batching at the incremental workload's scale, open loop.
+    S sessions (n = 2^24 each, Union-Early), each with its own stream of 2^28
+    RMAT insertions and 2^28 query pairs in batches of log-uniform size in
+    [10^3, 10^8] (host buffers).  Requests ARRIVE by a seeded Poisson process
+    per session at an offered load (ops/s, a fraction of what the plain loop
+    sustains back to back) and are either (plain) executed one at a time in
+    arrival order by synchronous gconn_inc_* calls, or (served) submitted at
+    arrival to one gconn_server, which admits them as slots and staging
+    memory free up and overlaps different sessions' work.  Latency is arrival
+    to answer on the host clock; every query answer must be identical."""
+    S = args.serve_sessions
+    n, trace = serving_trace(S, INC_N_SCALE, args.serve_ops, SEED_SERVE)
     v = g.make_variant(link="early")
-    # plain: one synchronous call per request
-    hs = [g.gconn_inc_create(n, v) for _ in range(S)]
-    torch.cuda.synchronize()
-    plain_ans = [[None] * R for _ in range(S)]
-    plain_lat = []
-    t0 = time.perf_counter()
-    for r in range(R):
-        for s in range(S):
-            op, a = streams[s][r]
-            t1 = time.perf_counter()
-            if op == g.GCONN_OP_INSERT:
+    total_ops = sum(len(a) for reqs in trace for _, a in reqs)
+    nreq = sum(len(r) for r in trace)
+
+    def plain_run(arrivals):
+        """One thread, arrival order; arrivals None = back to back."""
+        hs = [g.gconn_inc_create(n, v) for _ in range(S)]
+        torch.cuda.synchronize()
+        order = sorted((arrivals[s][r] if arrivals else 0.0, s, r) for s in range(S) for r in range(len(trace[s])))
+        answers = [[None] * len(trace[s]) for s in range(S)]
+        lat = []
+        t0 = time.perf_counter()
+        for at, s, r in order:
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            op, a = trace[s][r]
+            if op == 0:
                 g.gconn_inc_insert_batch(hs[s], len(a), a)
             else:
                 out = np.empty(len(a), np.uint8)
                 g.gconn_inc_query(hs[s], len(a), a, out)
-                plain_ans[s][r] = out
-            plain_lat.append((time.perf_counter() - t1) * 1e3)
-    plain_s = time.perf_counter() - t0
-    for h in hs:
-        g.gconn_inc_destroy(h)
-    # served
-    srv = g.gconn_server_create()
-    sids = [g.gconn_server_open_session(srv, n, v) for _ in range(S)]
-    served_ans = [[None] * R for _ in range(S)]
-    lats = [[] for _ in range(S)]
+                answers[s][r] = out
+            lat.append((time.perf_counter() - t0 - at) * 1e3)
+        span = time.perf_counter() - t0 - (order[0][0] if arrivals else 0.0)
+        for h in hs:
+            g.gconn_inc_destroy(h)
+        return answers, lat, span
 
-    def client(s):
-        ts = []
-        for r, (op, a) in enumerate(streams[s]):
-            out = np.empty(len(a), np.uint8) if op == g.GCONN_OP_QUERY else None
-            served_ans[s][r] = out
-            ts.append(g.gconn_server_submit(srv, sids[s], op, len(a), a, out))
-        lats[s] = [g.gconn_server_wait(srv, t) for t in ts]
-    th = [threading.Thread(target=client, args=(s,)) for s in range(S)]
-    t0 = time.perf_counter()
-    for t in th:
-        t.start()
-    for t in th:
-        t.join()
-    served_s = time.perf_counter() - t0
-    st = g.gconn_server_stats(srv)
-    g.gconn_server_destroy(srv)
-    same = all(served_ans[s][r] is None or bool((served_ans[s][r] == plain_ans[s][r]).all())
-               for s in range(S) for r in range(R))
-    all_lat = [x for l in lats for x in l]
-    return {"sessions": S, "requests": S * R, "ops": total_ops, "n_per_session": n,
-            "plain_ops_per_s": total_ops / plain_s, "served_ops_per_s": total_ops / served_s,
-            "speedup": round(plain_s / served_s, 2), "identical_answers": same,
-            "plain_latency_ms_p50": round(pct(plain_lat, 50), 3), "plain_latency_ms_p99": round(pct(plain_lat, 99), 3),
-            "served_latency_ms_p50": round(pct(all_lat, 50), 3), "served_latency_ms_p99": round(pct(all_lat, 99), 3),
-            "server_launches": st["launches"], "server_groups": st["groups"],
-            "latency": "host clock, submit to answers in the client's buffer (all requests submitted at once)",
-            "inputs": "host memory (pageable), copied through the server's pinned staging"}
+    def served_run(arrivals):
+        srv = g.gconn_server_create()
+        sids = [g.gconn_server_open_session(srv, n, v) for _ in range(S)]
+        answers = [[None] * len(trace[s]) for s in range(S)]
+        lat = [[] for _ in range(S)]
+        done = [0.0] * S
+        tickets = [[] for _ in range(S)]
+        cv = threading.Condition()
+        t0 = time.perf_counter()
+
+        def submitter(s):
+            for r, (op, a) in enumerate(trace[s]):
+                at = arrivals[s][r]
+                now = time.perf_counter() - t0
+                if at > now:
+                    time.sleep(at - now)
+                out = np.empty(len(a), np.uint8) if op == 1 else None
+                answers[s][r] = out
+                lag = (time.perf_counter() - t0 - at) * 1e3
+                t = g.gconn_server_submit(srv, sids[s], g.GCONN_OP_INSERT if op == 0 else g.GCONN_OP_QUERY,
+                                          len(a), a, out)
+                with cv:
+                    tickets[s].append((t, lag))
+                    cv.notify_all()
+
+        def waiter(s):
+            for r in range(len(trace[s])):
+                with cv:
+                    cv.wait_for(lambda: len(tickets[s]) > r)
+                    t, lag = tickets[s][r]
+                lat[s].append(g.gconn_server_wait(srv, t) + lag)
+            done[s] = time.perf_counter() - t0
+
+        th = [threading.Thread(target=f, args=(s,)) for s in range(S) for f in (submitter, waiter)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        st = g.gconn_server_stats(srv)
+        g.gconn_server_destroy(srv)
+        span = max(done) - min(arrivals[s][0] for s in range(S))
+        return answers, [x for l in lat for x in l], span, st
+
+    # the plain loop back to back: its capacity sets the offered loads
+    ref_answers, _, span0 = plain_run(None)
+    cap_ops = total_ops / span0
+    rng = np.random.default_rng(SEED_SERVE)
+    rows, identical = [], True
+    for frac in [float(x) for x in args.serve_loads.split(",")]:
+        rate = frac * cap_ops                                   # offered ops/s, all sessions
+        arrivals = []
+        for s in range(S):                                      # Poisson, mean request size per session
+            mean_ops = sum(len(a) for _, a in trace[s]) / len(trace[s])
+            gaps = rng.exponential(mean_ops * S / rate, len(trace[s]))
+            arrivals.append(list(np.cumsum(gaps)))
+        pa, pl, ps = plain_run(arrivals)
+        sa, sl, ss, st = served_run(arrivals)
+        same = all((sa[s][r] is None) or bool(np.array_equal(sa[s][r], ref_answers[s][r]))
+                   for s in range(S) for r in range(len(trace[s])))
+        same = same and all((pa[s][r] is None) or bool(np.array_equal(pa[s][r], ref_answers[s][r]))
+                            for s in range(S) for r in range(len(trace[s])))
+        identical &= same
+        rows.append({"offered_load_of_plain_capacity": frac, "offered_ops_per_s": rate,
+                     "plain": {"ops_per_s": total_ops / ps, "latency_ms_p50": round(pct(pl, 50), 3),
+                               "latency_ms_p99": round(pct(pl, 99), 3)},
+                     "served": {"ops_per_s": total_ops / ss, "latency_ms_p50": round(pct(sl, 50), 3),
+                                "latency_ms_p99": round(pct(sl, 99), 3), "launches": st["launches"],
+                                "groups": st["groups"]},
+                     "identical_answers": same})
+    return {"sessions": S, "n_per_session": n, "requests": nreq, "ops": total_ops,
+            "ops_per_session": args.serve_ops, "batch_law": "log-uniform sizes in [1e3, 1e8], insert then query",
+            "plain_capacity_ops_per_s": cap_ops, "loads": rows, "identical_answers": identical,
+            "arrivals": "open loop: seeded Poisson per session at the offered load",
+            "latency": "host clock, arrival to answers in the client's buffer",
+            "inputs": "host memory (pageable)"}
 
 
 def cpu_model() -> str:
@@ -1183,6 +1255,64 @@ def run_edge_inspect(args):
                               "ms": round(a.elapsed_time(z), 3)}), flush=True)
 
 
+def run_inc_probe(args):
+    """One insert batch and one query batch of args.inc_probe pairs on an
+    n = 2^24 handle that already holds the first 2^27 edges of the RMAT
+    scale-24 insert stream (a realistic forest): the launches a kernel
+    profile of the incremental path captures (the prefix is the first
+    insert launch, the probe batch the second)."""
+    import torch
+    import paper_2008_11839_gb300 as g
+    g.build()
+    dev = torch.device("cuda", 0)
+    n = 1 << INC_N_SCALE
+    perm = graphgen.permutation(n, SEED_INC, 6)
+    pre, b = 1 << 27, args.inc_probe
+    e = rmat_stream(INC_N_SCALE, pre + b, SEED_INC, perm)
+    d_e = torch.from_numpy(e.view(np.int32)).to(dev)
+    q = torch.from_numpy(graphgen.pairs_range(n, 0, b, SEED_INC).view(np.int32)).to(dev)
+    out = torch.empty(b, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    # the eager initialisation a handle pays once (P[v] = v over n = 2^24):
+    # the cost a lazy per-vertex initialisation would trade for a check on
+    # every access
+    init_ms = []
+    for _ in range(6):
+        g.gconn_profile_reset()
+        g.gconn_profile_select("init")
+        g.gconn_profile_enable(True)
+        h = g.Incremental(n, parse_variant(g, "none/early/naive"), stream)
+        g.gconn_profile_enable(False)
+        g.gconn_profile_select(None)
+        torch.cuda.synchronize()
+        g.gconn_profile_sync()
+        prof = g.gconn_profile_get()
+        h.close()
+        if "init" in prof:
+            init_ms.append(prof["init"][1])
+    g.gconn_profile_reset()
+    print(json.dumps({"eager_init": {"n": n, "ms_median": round(float(np.median(init_ms[1:])), 4) if init_ms else None,
+                                     "bytes": 4 * n, "runs": len(init_ms) - 1}}), flush=True)
+    rows = []
+    for spec in args.inc_probe_variants.split(","):
+        inc = g.Incremental(n, parse_variant(g, "none/" + spec), stream)
+        inc.insert(d_e[:pre], stream)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        inc.insert(d_e[pre:pre + b], stream)
+        ev[1].record(stream)
+        inc.query(q, out, stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        g.gconn_sync(stream)
+        inc.close()
+        ti, tq = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        rows.append({"variant": spec, "batch": b, "insert_ms": round(ti, 4), "query_ms": round(tq, 4),
+                     "updates_per_s": b / (ti * 1e-3), "queries_per_s": b / (tq * 1e-3)})
+        print(json.dumps(rows[-1]), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1200,6 +1330,13 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-forest", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inc-probe", type=int, default=0,
+                    help="time one insert and one query batch of this size after a 2^27-edge prefix")
+    ap.add_argument("--inc-probe-variants", default="early/naive")
+    ap.add_argument("--serve-sessions", type=int, default=2)
+    ap.add_argument("--serve-ops", type=int, default=1 << 28, help="insertions (and queries) per serving session")
+    ap.add_argument("--serve-loads", default="0.3,0.6,0.9,1.2",
+                    help="offered loads as fractions of the plain loop's back-to-back throughput")
     ap.add_argument("--no-c1", action="store_true", help="skip the ER n=65,536 COO leg")
     ap.add_argument("--no-c3", action="store_true", help="skip the grid + paths leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -1241,6 +1378,9 @@ def main():
         return
     if args.edge_inspect:
         run_edge_inspect(args)
+        return
+    if args.inc_probe:
+        run_inc_probe(args)
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)

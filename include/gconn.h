@@ -101,7 +101,8 @@ typedef struct gconn_variant {
     int32_t find;       /* GCONN_FIND_* */
     int32_t splice;     /* GCONN_SPLICE_* (Union-Rem-CAS / Union-Rem-Lock only) */
     int32_t lt_rules;   /* GCONN_LT_* bits (Liu-Tarjan only) */
-    int32_t block;      /* threads per block, 0 = library default */
+    int32_t block;      /* threads per block of the finish kernels, 0 = library default (256);
+                           a multiple of 32 in [64, 1024], values above 256 run as 256 */
     uint64_t seed;      /* L_max / BFS-source sampling and Union-JTB priorities */
     uint32_t iter_cap;  /* per-operation loop cap, 0 = default (2^24) */
     uint32_t ablation;  /* 0 = the library's kernels; GCONN_ABL_* bits select plain forms

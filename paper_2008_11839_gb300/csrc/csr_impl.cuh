@@ -61,7 +61,9 @@ gconn_status dispatch_uf(int L, int F, int S, bool SF, Fn&& fn) {
     return GCONN_E_UNSUPPORTED;
 }
 
-inline int block_of(const Variant& v) { return v.block > 0 ? v.block : 256; }
+// Threads per block of the finish kernels: the variant's choice, at most 256
+// (their launch bounds).
+inline int block_of(const Variant& v) { return v.block > 0 && v.block < 256 ? v.block : 256; }
 
 // ---------------------------------------------------------------- CSR path
 struct CsrScratch {
@@ -217,7 +219,7 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const OffT* off, co
     if (rounds) { sv.link = GCONN_LINK_ASYNC; sv.find = GCONN_FIND_NAIVE; sv.splice = 0; }
     bool jtb = sv.link == GCONN_LINK_JTB;
     bool vec = !jtb && ((uintptr_t)off & 15u) == 0 && ((uintptr_t)s.P & 15u) == 0;
-    bool tail = vec && !rounds && !stats && !(v.ablation & GCONN_ABL_NO_VG) && (v.block <= 0 || v.block == TAIL_BLOCK);
+    bool tail = vec && !rounds && !stats && !(v.ablation & GCONN_ABL_NO_VG) && block_of(v) == TAIL_BLOCK;
     // the deferred-union kernel leaves the sampled mode for the tail
     bool mode = tail && (v.sample == GCONN_SAMPLE_KOUT || hb_fused(sv, s));
     if (hb_fused(sv, s)) {   // InitLabel and HB step 1 in one pass

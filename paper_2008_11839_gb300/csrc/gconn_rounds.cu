@@ -27,7 +27,10 @@ constexpr unsigned long long NOMSG = 0xFFFFFFFFFFFFFFFFull;
 constexpr uint32_t MAX_ROUNDS = 1u << 16;   // round cap: E_NONCONVERGED beyond it
 constexpr int RB = 256;                     // block size of the round kernels
 
-// Control words of one round kernel, zeroed before its launch.
+// Control words of one round kernel, zeroed before its launch.  chg only
+// grows: after round r's last barrier every block reads it, and it is at
+// least r + 1 exactly when round r changed something (a block that already
+// went on to round r + 1 can only have raised it further).
 struct RoundCtl {
     GridBar bar;
     uint32_t chg;      // 1 + the last round in which something changed
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(RB) k_sv(const uint2* __restrict__ E, const ui
         }
         compress_copy(n, P, prev, err);
         if (!grid_sync(&ctl->bar, err)) return;
-        if (__ldcg(&ctl->chg) != r + 1) {
+        if (__ldcg(&ctl->chg) < r + 1) {   // no change in round r (chg only grows)
             finish_rounds(ctl, r + 1);
             return;
         }
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(RB) k_lt(const uint2* __restrict__ E_in, uint2
             mark_changed(ch, &ctl->chg, r);
             if (!grid_sync(&ctl->bar, err)) return;
         }
-        if (__ldcg(&ctl->chg) != r + 1) {
+        if (__ldcg(&ctl->chg) < r + 1) {   // no change in round r (chg only grows)
             finish_rounds(ctl, r + 1);
             break;
         }
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(RB) k_lp(const uint2* __restrict__ E, uint64_t
         }
         mark_changed(ch, &ctl->chg, r);
         if (!grid_sync(&ctl->bar, err)) return;
-        if (__ldcg(&ctl->chg) != r + 1) {
+        if (__ldcg(&ctl->chg) < r + 1) {   // no change in round r (chg only grows)
             finish_rounds(ctl, r + 1);
             break;
         }
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(RB) k_stergiou(const uint2* __restrict__ E, ui
         }
         mark_changed(ch, &ctl->chg, r);
         if (!grid_sync(&ctl->bar, err)) return;
-        if (__ldcg(&ctl->chg) != r + 1) {
+        if (__ldcg(&ctl->chg) < r + 1) {   // no change in round r (chg only grows)
             finish_rounds(ctl, r + 1);
             break;
         }

@@ -88,6 +88,100 @@ static __global__ void __launch_bounds__(256) k_union_coo(const uint2* __restric
     }
 }
 
+// COO finish with Union-Rem-CAS, naive find and SplitAtomicOne (the library
+// default), K unions in flight per thread.  Every union is a chain of
+// dependent steps -- load both parents, then either a CAS that links a root
+// or one split step that loads a grandparent -- and one union per thread
+// leaves the memory system waiting on one chain per thread.  Here a thread
+// keeps K unions open as small state machines: each loop iteration issues
+// the pending memory operation of every open union, then consumes the
+// results and decides each one's next step; a finished union's slot takes
+// the thread's next edge.  Each union runs exactly the steps of
+// union_remcas<FD_NAIVE, SP_SPLIT_ONE> (same carried values, same CASes).
+enum : uint8_t { SL_IDLE = 0, SL_INIT = 1, SL_CAS = 2, SL_SPLIT = 3 };
+
+template <int K, bool SF>
+static __global__ void __launch_bounds__(256) k_union_coo_rem(const uint2* __restrict__ E, uint64_t m, UFState s,
+                                                              uint32_t eid_base) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t next = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t* P = s.P;
+    uint32_t ru[K], rv[K], pu[K], pv[K], eid[K], left[K], a[K], b[K];
+    uint8_t op[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) op[k] = SL_IDLE;
+    uint32_t it = 0;
+    while (true) {
+        if ((++it & 63u) == 0 && err_abort(s.err)) return;
+        bool open = false;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {        // refill idle slots with the thread's next edges
+            while (op[k] == SL_IDLE && next < m) {
+                uint2 e = __ldcs(E + next);
+                uint64_t i = next;
+                next += stride;
+                if (e.x >= s.n || e.y >= s.n) {
+                    atomicOr(s.err, GC_DERR_RANGE);
+                    continue;
+                }
+                if (e.x == e.y) continue;
+                ru[k] = e.x;
+                rv[k] = e.y;
+                eid[k] = eid_base + (uint32_t)i;
+                left[k] = s.cap;
+                op[k] = SL_INIT;
+            }
+            open |= op[k] != SL_IDLE;
+        }
+        if (!open) return;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {        // issue: one memory operation per open union
+            if (op[k] == SL_INIT) {
+                a[k] = ldq<true>(P, ru[k]);
+                b[k] = ldq<true>(P, rv[k]);
+            } else if (op[k] == SL_CAS) {
+                a[k] = atomicCAS(P + ru[k], ru[k], pv[k]);
+            } else if (op[k] == SL_SPLIT) {
+                a[k] = ldq<true>(P, pu[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {        // consume, then choose the next step
+            if (op[k] == SL_IDLE) continue;
+            if (op[k] == SL_INIT) {
+                pu[k] = a[k];
+                pv[k] = b[k];
+            } else if (op[k] == SL_CAS) {
+                if (a[k] == ru[k]) {         // linked r_u under P[r_v]
+                    if (SF) s.sf[ru[k]] = eid[k];
+                    op[k] = SL_IDLE;
+                    continue;
+                }
+                pu[k] = a[k];                // r_u was linked meanwhile: its fresh parent
+            } else {                         // one split step: P[r_u] <- grandparent
+                uint32_t w = a[k];
+                if (w != pu[k]) atomicCAS(P + ru[k], pu[k], w);
+                ru[k] = pu[k];
+                pu[k] = w;
+            }
+            if (op[k] != SL_INIT && --left[k] == 0) {
+                atomicOr(s.err, GC_DERR_NONCONV);
+                op[k] = SL_IDLE;
+                continue;
+            }
+            if (pu[k] == pv[k]) {            // same set
+                op[k] = SL_IDLE;
+                continue;
+            }
+            if (pu[k] < pv[k]) {
+                uint32_t t = ru[k]; ru[k] = rv[k]; rv[k] = t;
+                t = pu[k]; pu[k] = pv[k]; pv[k] = t;
+            }
+            op[k] = ru[k] == pu[k] ? SL_CAS : SL_SPLIT;
+        }
+    }
+}
+
 // k-out sampling (Algorithm 2, first k edges of every vertex).  A warp takes
 // 32 consecutive vertices, reads their first k <= KOUT_WARP_K column entries
 // (one sector per row), and packs one job per vertex with a sampled arc into

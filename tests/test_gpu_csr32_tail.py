@@ -146,7 +146,7 @@ def test_lmax_root_moved_in_finish(sample, aligned):
             assert st.lmax == 3 and st.active_vertices == 3
 
 
-@pytest.mark.parametrize("block", [128, 512])
+@pytest.mark.parametrize("block", [128, 192])
 def test_other_finish_block_sizes(block):
     """A finish block size other than the fused pass's takes the multi-kernel pass."""
     v = g.make_variant(sample="kout", link="remcas", splice="split_one", block=block)
