@@ -45,7 +45,7 @@ DEFAULT_VARIANT = "kout/remcas/naive/split_one"
 # DRAM bytes (read + write) of one k_kout launch per vertex, from an ncu capture
 # of the default variant at RMAT scale 20, edge factor 16 (41.984 MB read +
 # 0.383 MB written, / 2^20); valid while that kernel is unchanged.
-KOUT_DRAM_BYTES_PER_VERTEX = None     # re-captured after the uint32-offset k_kout
+KOUT_DRAM_BYTES_PER_VERTEX = 38.268416e6 / 2 ** 20   # uint32 offsets: 37.789 MB read + 0.479 MB written
 KOUT_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_kout launch at RMAT scale 20 "
                     "(same variant and edge factor), scaled by the vertex count")
 
@@ -172,8 +172,6 @@ def alg_bytes(name: str, st: dict):
         return 4 * st.get("active_arcs", 0) + 8 * st.get("active_vertices", 0)
     if name in ("compress", "finalize"):
         return 8 * n
-    if name == "tail":           # gathering + finish + finalisation in one launch
-        return 4 * n + 4 * st.get("active_arcs", 0) + 8 * st.get("active_vertices", 0) + 8 * n
     if name == "union_coo":
         return 8 * st["m"]
     return None
@@ -423,9 +421,21 @@ def run_ours(args, rank, world, local_rank):
             g.gconn_cc_csr32(n, h_off, h_cols, h_lab, v, stream)   # H2D + kernels + D2H + sync
             tt.append(time.perf_counter() - t1)
         e2e_s = float(np.mean(tt))
+        lab_e2e = h_lab.numpy().view(np.uint32)
+        staged = os.environ.get("GCONN_HOST_STAGE") == "1"
+        # the offsets are copied; the columns are read in place where the
+        # device reads host memory (k per row by the sampling, the active rows
+        # by the finish), else copied whole
+        in_place = 0 if staged else 4 * 2 * n + 4 * st.get("active_arcs", 0)
+        copied = int(off32.nbytes + (cols.nbytes if staged else 0))
         result["e2e"] = {"value": M / e2e_s, "unit": "edges/s",
-                         "h2d_bytes_per_step": int(off32.nbytes + cols.nbytes),
-                         "d2h_bytes_per_step": int(4 * n), "ms_per_step": round(e2e_s * 1e3, 4)}
+                         "h2d_bytes_per_step": copied + in_place,
+                         "d2h_bytes_per_step": int(4 * n), "ms_per_step": round(e2e_s * 1e3, 4),
+                         "h2d_breakdown": {"copied": copied, "read_in_place": in_place,
+                                           "note": "columns read in place over the host link (cache-line "
+                                                   "granularity: the link moves more than these algorithmic "
+                                                   "bytes)" if not staged else "all inputs copied"},
+                         "labels_equal_device_pass": bool(np.array_equal(lab_e2e, lab_timed))}
 
     legs = {"rmat_s22": (n, e, lab_timed)}      # final labels, checked against the oracle below
     roof_args = (hbm, peak_src)

@@ -76,8 +76,8 @@ inline bool hb_fused(const Variant& v, const UFState& s) {
     return v.sample == GCONN_SAMPLE_HB && v.link != GCONN_LINK_JTB && v.hb_n <= HB_WARP_N && !s.W;
 }
 
-// With mode_dev set (the fused tail follows), the deferred-union kernel writes
-// the sampled mode label there instead of L_max.
+// mode_dev: a scratch word for the samples' mode label, taken by block 0 of
+// the deferred-union kernel while the other blocks run the deferred unions.
 template <class OffT>
 gconn_status csr_sample(const Variant& v, const UFState& s, const OffT* off, const uint32_t* cols,
                         uint32_t* lmax_dev, unsigned long long* dq_count, uint32_t* lmax_done, uint32_t* mode_dev,
@@ -99,13 +99,10 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const OffT* off, con
             GC_TRY(launch_pdl("kout", k, grid_for(k, KOUT_BLOCK, n), KOUT_BLOCK, 0, st, off, cols, v.k, s, dq,
                               (v.ablation & GCONN_ABL_PLAIN_SAMPLE) != 0));
             auto kj = k_union_jobs<l, f, sp, w>;
-            // the last block of the retry kernel also computes L_max (or its
-            // block 0 the sampled mode, for the fused tail)
-            if (mode_dev)
-                return launch_pdl("kout_deferred", kj, std::max(2u, grid_for(kj, LMAX_SAMPLES, qcap)), LMAX_SAMPLES,
-                                  0, st, s, dq, v.seed, (uint32_t*)nullptr, (uint32_t*)nullptr, mode_dev);
-            return launch_pdl("kout_deferred", kj, grid_for(kj, LMAX_SAMPLES, qcap), LMAX_SAMPLES, 0, st, s, dq,
-                              v.seed, lmax_dev, lmax_done, (uint32_t*)nullptr);
+            // the retry kernel also yields L_max (block 0: the samples' mode,
+            // the last block: its root)
+            return launch_pdl("kout_deferred", kj, std::max(2u, grid_for(kj, LMAX_SAMPLES, qcap)), LMAX_SAMPLES, 0, st, s,
+                              dq, v.seed, lmax_dev, lmax_done, mode_dev);
         }));
         return GCONN_OK;
     } else if (hb_fused(v, s)) {   // step 1 already done by k_hb_init
@@ -117,13 +114,10 @@ gconn_status csr_sample(const Variant& v, const UFState& s, const OffT* off, con
             auto k = k_hb2w<l, f, sp, w, OffT>;
             GC_TRY(launch_pdl("hb2", k, grid_for(k, 256, n), 256, 0, st, off, cols, v.hb_n, s, dq));
             auto kj = k_union_jobs<l, f, sp, w>;
-            // the last block of the retry kernel also computes L_max (or its
-            // block 0 the sampled mode, for the fused tail)
-            if (mode_dev)
-                return launch_pdl("hb_deferred", kj, std::max(2u, grid_for(kj, LMAX_SAMPLES, qcap)), LMAX_SAMPLES,
-                                  0, st, s, dq, v.seed, (uint32_t*)nullptr, (uint32_t*)nullptr, mode_dev);
-            return launch_pdl("hb_deferred", kj, grid_for(kj, LMAX_SAMPLES, qcap), LMAX_SAMPLES, 0, st, s, dq,
-                              v.seed, lmax_dev, lmax_done, (uint32_t*)nullptr);
+            // the retry kernel also yields L_max (block 0: the samples' mode,
+            // the last block: its root)
+            return launch_pdl("hb_deferred", kj, std::max(2u, grid_for(kj, LMAX_SAMPLES, qcap)), LMAX_SAMPLES, 0, st, s,
+                              dq, v.seed, lmax_dev, lmax_done, mode_dev);
         });
     } else if (v.sample == GCONN_SAMPLE_HB) {
         GC_TRY(launch("hb1", k_hb1<OffT>, grid_for(k_hb1<OffT>, 256, n), 256, 0, st, off, cols, n, s.P, s.sf,
@@ -191,12 +185,6 @@ static __global__ void k_sample_stats(const OffT* __restrict__ off, const uint32
 
 // With `finalized` non-null, a union-find finish also finalises the labels in
 // P (from the gathered lists, k_finalize_gathered) and sets *finalized.
-//
-// The usual union-find pass (no counting, no ablation, no Union-JTB or round
-// finish, 16-byte aligned offsets and parents, the default finish block)
-// runs gathering, finish and finalisation as one cooperative launch of
-// k_tail; its L_max is the root of the sampled mode label (k-out / HB, from
-// the deferred-union kernel) or of BFS's L_max.
 template <class OffT>
 gconn_status csr_connect(const Variant& v, const UFState& s, const OffT* off, const uint32_t* cols,
                          cudaStream_t st, CsrStats* stats = nullptr, bool* finalized = nullptr) {
@@ -205,9 +193,9 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const OffT* off, co
     CsrScratch sc;
     bool sampled = v.sample != GCONN_SAMPLE_NONE;
     // the pass's counters in one 64-byte header, cleared by the init kernel:
-    // [0] L_max, [1..3] gathering counters, [4] sampled mode label,
+    // [0] L_max, [1..3] gathering counters, [4] the samples' mode label,
     // [8..9] deferred-union count (u64), [10] blocks of the retry kernel done
-    // (the last one computes L_max), [12..13] the fused tail's grid barrier
+    // (the last one resolves L_max)
     GC_TRY(sc.counters.alloc(16 * sizeof(uint32_t), st));
     uint32_t* hdr = sc.counters.as<uint32_t>();
     uint32_t* lmax = sampled ? hdr : nullptr;
@@ -218,17 +206,13 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const OffT* off, co
     bool rounds = is_rounds_link(v.link);
     if (rounds) { sv.link = GCONN_LINK_ASYNC; sv.find = GCONN_FIND_NAIVE; sv.splice = 0; }
     bool jtb = sv.link == GCONN_LINK_JTB;
-    bool vec = !jtb && ((uintptr_t)off & 15u) == 0 && ((uintptr_t)s.P & 15u) == 0;
-    bool tail = vec && !rounds && !stats && !(v.ablation & GCONN_ABL_NO_VG) && block_of(v) == TAIL_BLOCK;
-    // the deferred-union kernel leaves the sampled mode for the tail
-    bool mode = tail && (v.sample == GCONN_SAMPLE_KOUT || hb_fused(sv, s));
     if (hb_fused(sv, s)) {   // InitLabel and HB step 1 in one pass
         GC_TRY(launch_pdl("init", k_hb_init<OffT>, grid_for(k_hb_init<OffT>, 256, n), 256, 0, st, off, cols, n, s.P,
                           s.H, s.sf, s.err, hdr, 16u));
     } else {
         GC_TRY(init_state(s, st, hdr, 16));
     }
-    if (sampled) GC_TRY(csr_sample(sv, s, off, cols, lmax, dq_count, hdr + 10, mode ? hdr + 4 : nullptr, st));
+    if (sampled) GC_TRY(csr_sample(sv, s, off, cols, lmax, dq_count, hdr + 10, hdr + 4, st));
     if (v.ablation & GCONN_ABL_NO_VG) {   // measurement form: full compression, then the plain finish
         if (rounds || sv.link == GCONN_LINK_JTB || stats) return GCONN_E_UNSUPPORTED;
         GC_TRY(compress_all(sv, s, st));
@@ -255,20 +239,7 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const OffT* off, co
     uint32_t* small = sc.small.as<uint32_t>();
     unsigned long long* tasks = sc.tasks.as<unsigned long long>();
     uint32_t* over = sc.over.as<uint32_t>();
-    int L, F, S;
-    uf_triple(v, &L, &F, &S);
-    int B = block_of(v);
-    if (tail) {
-        const uint32_t* mode_p = !sampled ? nullptr : mode ? hdr + 4 : hdr;
-        GC_TRY(dispatch_uf(L, F, S, s.sf != nullptr, [&]<int l, int f, int sp, bool w>() {
-            auto k = k_tail<l, f, sp, w, OffT>;
-            return launch_coop("tail", k, grid_for(k, TAIL_BLOCK, ((uint64_t)n + 3) / 4), TAIL_BLOCK, 0, st, off,
-                               cols, s, hdr, mode_p, active, small, tasks, (uint32_t)task_cap, over,
-                               finalized ? 1 : 0);
-        }));
-        if (finalized) *finalized = true;
-        return GCONN_OK;
-    }
+    bool vec = !jtb && ((uintptr_t)off & 15u) == 0 && ((uintptr_t)s.P & 15u) == 0;
     {
         auto k = jtb ? k_vg<LK_JTB, true, OffT> : vec ? k_vg4<LK_ASYNC, OffT> : k_vg<LK_ASYNC, true, OffT>;
         GC_TRY(launch_pdl("vg", k, grid_for(k, 256, vec ? ((uint64_t)n + 3) / 4 : (uint64_t)n), 256, 0, st, off, s,
@@ -284,6 +255,9 @@ gconn_status csr_connect(const Variant& v, const UFState& s, const OffT* off, co
     }
     if (rounds) return rounds_csr(v, s, off, cols, active, small, cnt + 0, tasks, cnt + 1, (uint32_t)task_cap,
                                   over, cnt + 2, st);
+    int L, F, S;
+    uf_triple(v, &L, &F, &S);
+    int B = block_of(v);
     GC_TRY(dispatch_uf(L, F, S, s.sf != nullptr, [&]<int l, int f, int sp, bool w>() {
         auto k = k_finish<l, f, sp, w, OffT>;
         return launch_pdl("finish", k, grid_for(k, B, (uint64_t)n * 32), B, 0, st, off, cols, s,
@@ -344,7 +318,12 @@ static gconn_status static_run(uint32_t n, uint64_t m, const uint32_t* edges, co
         if (m) {
             bool h = !is_device_ptr(edges);
             any_host |= h;
-            GC_TRY(stage_in(edges, sizeof(uint32_t) * 2 * m, st, ebuf, (const void**)&d_edges));
+            // a union-find finish reads every edge once: host edges are read
+            // in place where the device can; the round finishes re-read them
+            if (is_rounds_link(v.link))
+                GC_TRY(stage_in(edges, sizeof(uint32_t) * 2 * m, st, ebuf, (const void**)&d_edges));
+            else
+                GC_TRY(stage_in_once(edges, sizeof(uint32_t) * 2 * m, st, ebuf, (const void**)&d_edges));
         }
     } else {
         OffT narcs = 0;
@@ -360,19 +339,18 @@ static gconn_status static_run(uint32_t n, uint64_t m, const uint32_t* edges, co
         if (oh) {
             narcs = off[n];
             any_host = true;
+            // offsets are read by several kernels: staged; the columns are read
+            // in place where the device can (sampling reads k per row, the
+            // finish only the active rows)
             GC_TRY(stage_in(off, sizeof(OffT) * ((size_t)n + 1), st, obuf, (const void**)&d_off));
-            if (narcs) {
-                if (is_device_ptr(cols)) {
-                    d_cols = cols;
-                } else {
-                    GC_TRY(stage_in(cols, sizeof(uint32_t) * (uint64_t)narcs, st, cbuf, (const void**)&d_cols));
-                }
-            }
+            if (narcs)
+                GC_TRY(stage_in_once(cols, sizeof(uint32_t) * (uint64_t)narcs, st, cbuf, (const void**)&d_cols));
         } else if (!is_device_ptr(cols)) {
             GC_CUDA(cudaMemcpyAsync(&narcs, off + n, sizeof(OffT), cudaMemcpyDeviceToHost, st));
             GC_CUDA(cudaStreamSynchronize(st));
             any_host = true;
-            if (narcs) GC_TRY(stage_in(cols, sizeof(uint32_t) * (uint64_t)narcs, st, cbuf, (const void**)&d_cols));
+            if (narcs)
+                GC_TRY(stage_in_once(cols, sizeof(uint32_t) * (uint64_t)narcs, st, cbuf, (const void**)&d_cols));
         }
     }
     // parent array: the caller's labels buffer when it is device memory

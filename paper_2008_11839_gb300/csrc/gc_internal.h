@@ -209,4 +209,14 @@ struct CsrArcsHint {
 // Staging of possibly-host arrays onto the device.
 gconn_status stage_in(const void* src, size_t bytes, cudaStream_t st, DevBuf& buf, const void** dev);
 
+// A device-usable address for host memory that kernels can read in place:
+// page-locked memory (its device mapping), or pageable memory on a device
+// that accesses pageable memory coherently (cudaDevAttrPageableMemoryAccess:
+// through the host's page tables on NVLink-C2C systems); nullptr otherwise,
+// or when the environment sets GCONN_HOST_STAGE=1 (always copy).
+const void* host_direct(const void* p);
+// For an array a pass reads once, or only in part: device memory as is, host
+// memory in place when host_direct allows it, else a staged copy.
+gconn_status stage_in_once(const void* src, size_t bytes, cudaStream_t st, DevBuf& buf, const void** dev);
+
 }  // namespace gc

@@ -134,6 +134,51 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+static int pageable_access() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return 0;
+    static std::atomic<int> cached[MAX_DEV];   // 0 unknown, 1 no, 2 yes
+    int c = cached[dev].load();
+    if (c == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+            cudaGetLastError();
+            v = 0;
+        }
+        c = v ? 2 : 1;
+        cached[dev].store(c);
+    }
+    return c == 2;
+}
+
+const void* host_direct(const void* p) {
+    static const bool staged = [] {
+        const char* e = getenv("GCONN_HOST_STAGE");
+        return e && e[0] == '1';
+    }();
+    if (!p || staged) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;           // page-locked: its device mapping
+    if (a.type == cudaMemoryTypeUnregistered && pageable_access()) return p;
+    return nullptr;
+}
+
+gconn_status stage_in_once(const void* src, size_t bytes, cudaStream_t st, DevBuf& buf, const void** dev) {
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return GCONN_OK;
+    }
+    if (const void* d = host_direct(src)) {
+        *dev = d;
+        return GCONN_OK;
+    }
+    return stage_in(src, bytes, st, buf, dev);
+}
+
 gconn_status DevBuf::alloc(size_t bytes, cudaStream_t stream) {
     release();
     st = stream;

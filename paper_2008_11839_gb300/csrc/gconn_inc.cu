@@ -218,7 +218,12 @@ extern "C" gconn_status gconn_inc_insert_batch(gconn_inc* h, uint64_t b, const u
     DevBuf eb;
     const uint32_t* de = nullptr;
     bool host = !is_device_ptr(edges);
-    GC_TRY(stage_in(edges, sizeof(uint32_t) * 2 * b, st, eb, (const void**)&de));
+    // a union-find finish reads the batch once (in place from host memory
+    // where the device can); the round finishes re-read it
+    if (is_rounds_link(h->v.link))
+        GC_TRY(stage_in(edges, sizeof(uint32_t) * 2 * b, st, eb, (const void**)&de));
+    else
+        GC_TRY(stage_in_once(edges, sizeof(uint32_t) * 2 * b, st, eb, (const void**)&de));
     UFState s = handle_state(h);
     uint64_t inspected = b;   // a union-find finish reads each edge of the batch once
     if (is_rounds_link(h->v.link)) {
@@ -244,7 +249,7 @@ extern "C" gconn_status gconn_inc_query(gconn_inc* h, uint64_t q, const uint32_t
     DevBuf pb, ob;
     const uint32_t* dp = nullptr;
     bool host_in = !is_device_ptr(pairs), host_out = !is_device_ptr(connected);
-    GC_TRY(stage_in(pairs, sizeof(uint32_t) * 2 * q, st, pb, (const void**)&dp));
+    GC_TRY(stage_in_once(pairs, sizeof(uint32_t) * 2 * q, st, pb, (const void**)&dp));   // read once
     uint8_t* dout = connected;
     if (host_out) {
         GC_TRY(ob.alloc(q, st));

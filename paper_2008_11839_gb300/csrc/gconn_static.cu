@@ -2,7 +2,6 @@
 // forest (Algorithms 1 and 2) over COO and CSR input.
 #include <cuda_runtime.h>
 #include <stdint.h>
-#include <stdlib.h>
 #include <string.h>
 
 #include "csr_impl.cuh"
@@ -47,31 +46,12 @@ gconn_status init_state(const UFState& s, cudaStream_t st, uint32_t* zero, uint3
     return launch_pdl("init", k_init, grid_for(k_init, 256, s.n), 256, 0, st, s.n, s.P, s.H, s.W, s.sf, zero, nzero);
 }
 
-// Unions in flight per thread in the Rem-CAS COO kernel: 1, 2 or 4
-// (GCONN_UNION_SLOTS; 1 = one union per thread, k_union_coo).
-static int union_slots() {
-    static int k = [] {
-        const char* e = getenv("GCONN_UNION_SLOTS");
-        int x = e ? atoi(e) : 4;
-        return (x == 1 || x == 2 || x == 4) ? x : 4;
-    }();
-    return k;
-}
-
 gconn_status union_coo(const Variant& v, const UFState& s, const uint32_t* edges, uint64_t m,
                        uint32_t eid_base, cudaStream_t st) {
     if (m == 0) return GCONN_OK;
     int L, F, S;
     uf_triple(v, &L, &F, &S);
     int B = block_of(v);
-    int K = union_slots();
-    if (L == LK_REMCAS && F == FD_NAIVE && S == SP_SPLIT_ONE && K > 1 && block_of(v) == 256) {
-        bool sf = s.sf != nullptr;
-        auto k = K == 2 ? (sf ? k_union_coo_rem<2, true> : k_union_coo_rem<2, false>)
-                        : (sf ? k_union_coo_rem<4, true> : k_union_coo_rem<4, false>);
-        return launch("union_coo", k, grid_for(k, 256, (m + K - 1) / K), 256, 0, st, (const uint2*)edges, m, s,
-                      eid_base);
-    }
     return dispatch_uf(L, F, S, s.sf != nullptr, [&]<int l, int f, int sp, bool sf>() {
         auto k = k_union_coo<l, f, sp, sf>;
         return launch("union_coo", k, grid_for(k, B, m), B, 0, st, (const uint2*)edges, m, s, eid_base);

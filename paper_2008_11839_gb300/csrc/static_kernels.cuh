@@ -88,100 +88,6 @@ static __global__ void __launch_bounds__(256) k_union_coo(const uint2* __restric
     }
 }
 
-// COO finish with Union-Rem-CAS, naive find and SplitAtomicOne (the library
-// default), K unions in flight per thread.  Every union is a chain of
-// dependent steps -- load both parents, then either a CAS that links a root
-// or one split step that loads a grandparent -- and one union per thread
-// leaves the memory system waiting on one chain per thread.  Here a thread
-// keeps K unions open as small state machines: each loop iteration issues
-// the pending memory operation of every open union, then consumes the
-// results and decides each one's next step; a finished union's slot takes
-// the thread's next edge.  Each union runs exactly the steps of
-// union_remcas<FD_NAIVE, SP_SPLIT_ONE> (same carried values, same CASes).
-enum : uint8_t { SL_IDLE = 0, SL_INIT = 1, SL_CAS = 2, SL_SPLIT = 3 };
-
-template <int K, bool SF>
-static __global__ void __launch_bounds__(256) k_union_coo_rem(const uint2* __restrict__ E, uint64_t m, UFState s,
-                                                              uint32_t eid_base) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    uint64_t next = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t* P = s.P;
-    uint32_t ru[K], rv[K], pu[K], pv[K], eid[K], left[K], a[K], b[K];
-    uint8_t op[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) op[k] = SL_IDLE;
-    uint32_t it = 0;
-    while (true) {
-        if ((++it & 63u) == 0 && err_abort(s.err)) return;
-        bool open = false;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {        // refill idle slots with the thread's next edges
-            while (op[k] == SL_IDLE && next < m) {
-                uint2 e = __ldcs(E + next);
-                uint64_t i = next;
-                next += stride;
-                if (e.x >= s.n || e.y >= s.n) {
-                    atomicOr(s.err, GC_DERR_RANGE);
-                    continue;
-                }
-                if (e.x == e.y) continue;
-                ru[k] = e.x;
-                rv[k] = e.y;
-                eid[k] = eid_base + (uint32_t)i;
-                left[k] = s.cap;
-                op[k] = SL_INIT;
-            }
-            open |= op[k] != SL_IDLE;
-        }
-        if (!open) return;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {        // issue: one memory operation per open union
-            if (op[k] == SL_INIT) {
-                a[k] = ldq<true>(P, ru[k]);
-                b[k] = ldq<true>(P, rv[k]);
-            } else if (op[k] == SL_CAS) {
-                a[k] = atomicCAS(P + ru[k], ru[k], pv[k]);
-            } else if (op[k] == SL_SPLIT) {
-                a[k] = ldq<true>(P, pu[k]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < K; ++k) {        // consume, then choose the next step
-            if (op[k] == SL_IDLE) continue;
-            if (op[k] == SL_INIT) {
-                pu[k] = a[k];
-                pv[k] = b[k];
-            } else if (op[k] == SL_CAS) {
-                if (a[k] == ru[k]) {         // linked r_u under P[r_v]
-                    if (SF) s.sf[ru[k]] = eid[k];
-                    op[k] = SL_IDLE;
-                    continue;
-                }
-                pu[k] = a[k];                // r_u was linked meanwhile: its fresh parent
-            } else {                         // one split step: P[r_u] <- grandparent
-                uint32_t w = a[k];
-                if (w != pu[k]) atomicCAS(P + ru[k], pu[k], w);
-                ru[k] = pu[k];
-                pu[k] = w;
-            }
-            if (op[k] != SL_INIT && --left[k] == 0) {
-                atomicOr(s.err, GC_DERR_NONCONV);
-                op[k] = SL_IDLE;
-                continue;
-            }
-            if (pu[k] == pv[k]) {            // same set
-                op[k] = SL_IDLE;
-                continue;
-            }
-            if (pu[k] < pv[k]) {
-                uint32_t t = ru[k]; ru[k] = rv[k]; rv[k] = t;
-                t = pu[k]; pu[k] = pv[k]; pv[k] = t;
-            }
-            op[k] = ru[k] == pu[k] ? SL_CAS : SL_SPLIT;
-        }
-    }
-}
-
 // k-out sampling (Algorithm 2, first k edges of every vertex).  A warp takes
 // 32 consecutive vertices, reads their first k <= KOUT_WARP_K column entries
 // (one sector per row), and packs one job per vertex with a sampled arc into
@@ -390,57 +296,50 @@ static __global__ void __launch_bounds__(LMAX_SAMPLES) k_lmax(UFState s, uint64_
 
 // Unions deferred by k_kout / k_hb2w, finished with the full cap from where
 // each abandoned climb stopped (see Spin).
-// Blocks of LMAX_SAMPLES threads.  With lmax_out set, the block that finishes
-// last (a counter taken after a fence; `done` must start at zero) also
-// computes L_max, one sample per thread, which needs every
-// union done: no block waits for another, the last one just does more work.
-// It reads parents through L2 only, since its own L1 may hold lines from
-// before other blocks' links.
-// With mode_out set instead, block 0 computes the most frequent root label
-// of the samples right away, while the other blocks run the deferred unions
-// (grids of at least two blocks): a label's root only moves down its own
-// set, so the fused tail kernel takes L_max = root(mode) once every union is
-// done -- the same choice of set without serialising 1,024 walks behind the
-// unions.
+// Blocks of LMAX_SAMPLES threads.  L_max needs every union done, so it is
+// resolved by the block that finishes last (a counter taken after a fence;
+// `done` must start at zero): no block waits for another, the last one just
+// does more work.  It reads parents through L2 only, since its own L1 may
+// hold lines from before other blocks' links.
+// With mode_tmp set (grids of at least two blocks), block 0 takes the most
+// frequent root label of the samples right away, while the other blocks run
+// the deferred unions, and the last block only walks that label to its root:
+// a label's root only moves down its own set, so L_max = root(mode) picks the
+// same set without serialising 1,024 walks behind the unions.  Otherwise the
+// last block computes the mode of the samples' final roots itself.
 template <int L, int F, int S, bool SF>
 static __global__ void __launch_bounds__(LMAX_SAMPLES) k_union_jobs(UFState s, JobQueue dq, uint64_t seed,
-                                                           uint32_t* lmax_out, uint32_t* done, uint32_t* mode_out) {
+                                                           uint32_t* lmax_out, uint32_t* done, uint32_t* mode_tmp) {
     pdl_entry();
     __shared__ LmaxSmem sm;
+    __shared__ bool last;
+    constexpr int LR = L == LK_JTB ? LK_JTB : LK_ASYNC;
     unsigned long long cnt = *dq.count;
     if (cnt > dq.cap) cnt = dq.cap;
-    uint64_t b0 = blockIdx.x, nb = gridDim.x;
-    if (mode_out && nb > 1) {
-        if (blockIdx.x == 0) {
-            block_lmax<L == LK_JTB ? LK_JTB : LK_ASYNC, false>(s, seed, mode_out, sm);
-            return;
+    const bool split = mode_tmp && gridDim.x > 1;
+    if (split && blockIdx.x == 0) {
+        block_lmax<LR, false>(s, seed, mode_tmp, sm);
+    } else {
+        uint64_t b0 = split ? blockIdx.x - 1 : blockIdx.x, nb = split ? gridDim.x - 1 : gridDim.x;
+        uint64_t stride = nb * blockDim.x;
+        for (uint64_t i = b0 * blockDim.x + threadIdx.x; i < cnt; i += stride) {
+            KoutJob jb = dq.jobs[i];
+            Spin sp(s.cap);
+            uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
         }
-        b0 -= 1;
-        nb -= 1;
-    }
-    uint64_t stride = nb * blockDim.x;
-    for (uint64_t i = b0 * blockDim.x + threadIdx.x; i < cnt; i += stride) {
-        KoutJob jb = dq.jobs[i];
-        Spin sp(s.cap);
-        uf_union<L, F, S, SF>(s, jb.u, jb.v, jb.eid, sp);
-    }
-    if (mode_out) {                    // a one-block grid: the mode after the unions
-        if (nb == gridDim.x) {
-            __syncthreads();
-            __threadfence();
-            block_lmax<L == LK_JTB ? LK_JTB : LK_ASYNC, false>(s, seed, mode_out, sm);
-        }
-        return;
     }
     if (!lmax_out) return;
-    __shared__ bool last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
-    block_lmax<L == LK_JTB ? LK_JTB : LK_ASYNC, false>(s, seed, lmax_out, sm);
+    if (split) {
+        if (threadIdx.x == 0) *lmax_out = uf_root<LR, false>(s, __ldcg(mode_tmp));
+        return;
+    }
+    block_lmax<LR, false>(s, seed, lmax_out, sm);
 }
 
 // HB sampling step 1 (Algorithm 3): P[v] = min(v, w) for the smallest
@@ -1152,44 +1051,6 @@ static __device__ __noinline__ bool grid_sync(GridBar* b, uint32_t* err) {
     }
     __syncthreads();
     return ok != 0;
-}
-
-// The CSR pass after sampling in one cooperative launch (every block
-// resident), phases separated by grid barriers: L_max = root(mode) (each
-// block walks it; the sampled mode label, or BFS's L_max, or none), then
-// vertex gathering with full compression (vg4_pass), barrier, the
-// load-balanced finish (finish_pass), barrier, and finalisation from the
-// gathered lists (finalize_gathered_pass).  The phases are those of
-// k_vg4 / k_finish / k_finalize_gathered; one launch instead of three saves
-// two grid launches and drains on a pass whose finish touches only the
-// ~10^3 vertices sampling left active.  Lists, counters and the bitmask are
-// read through L2 after a barrier (other blocks wrote them), and the
-// finalisation walks through L2 (the finish linked roots in other blocks).
-// hdr: [0] L_max (written here), [1..3] gathering counters, [12..13] the grid
-// barrier -- all zeroed by the init kernel.
-constexpr int TAIL_BLOCK = 256;
-
-template <int L, int F, int S, bool SF, class OffT>
-static __global__ void __launch_bounds__(TAIL_BLOCK) k_tail(const OffT* __restrict__ off,
-                                                            const uint32_t* __restrict__ cols, UFState s,
-                                                            uint32_t* hdr, const uint32_t* mode_p, uint32_t* active,
-                                                            uint32_t* small, unsigned long long* tasks,
-                                                            uint32_t task_cap, uint32_t* over, int finalize) {
-    GridBar* bar = reinterpret_cast<GridBar*>(hdr + 12);
-    __shared__ uint32_t s_lmax;
-    if (threadIdx.x == 0) s_lmax = mode_p ? uf_root<LK_ASYNC, false>(s, __ldcg(mode_p)) : GC_DINF;
-    __syncthreads();
-    const uint32_t lmax = s_lmax;
-    if (mode_p && blockIdx.x == 0 && threadIdx.x == 0) hdr[0] = lmax;
-    vg4_pass<L, OffT, true>(off, s, lmax, active, small, hdr + 1, tasks, task_cap, hdr + 2, over, hdr + 3);
-    if (!grid_sync(bar, s.err)) return;
-    const uint32_t cs = __ldcg(hdr + 1), co = __ldcg(hdr + 3);
-    uint32_t ct = __ldcg(hdr + 2);
-    if (ct > task_cap) ct = task_cap;
-    finish_pass<L, F, S, SF, OffT, true>(off, cols, s, active, small, cs, tasks, ct, over, co);
-    if (!finalize) return;
-    if (!grid_sync(bar, s.err)) return;
-    finalize_gathered_pass<false>(s, lmax, small, cs, tasks, ct, over, co);
 }
 
 // Union-JTB roots are not minimal: canonicalise through the root.

@@ -25,9 +25,3 @@ def test_roofline_fraction():
     assert abs(r["frac"] - 1174.40516 / 6770.5) < 1e-4
     assert r["unit"] == "GB/s" and r["bound"] == "hbm" and r["kernel"] == "pass"
 
-
-def test_fused_tail_terms():
-    n = 1 << 22
-    st = {"n": n, "m": 1 << 26, "k": 2, "active_vertices": 10, "active_arcs": 100}
-    assert bench.alg_bytes("tail", st) == (bench.alg_bytes("vg", st) + bench.alg_bytes("finish", st)
-                                           + bench.alg_bytes("finalize", st)) == 4 * n + 400 + 80 + 8 * n

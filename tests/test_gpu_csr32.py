@@ -1,8 +1,8 @@
 """CSR with uint32 offsets (gconn_cc_csr32, gconn_spanning_forest_csr32 and
-their plans) and the fused post-sampling pass (vertex gathering, finish and
-finalisation in one cooperative launch), against the oracle, bit-exact on
-canonical labels; the multi-kernel pass that unaligned buffers and other
-finish block sizes take is checked on the same inputs."""
+their plans) against the oracle, bit-exact on canonical labels, on the
+vectorised gathering path (16-byte aligned buffers) and the scalar one
+(unaligned labels), other finish block sizes, and a graph whose finish moves
+the L_max root (finalisation must then walk every vertex)."""
 import numpy as np
 import pytest
 
@@ -133,7 +133,7 @@ def test_lmax_root_moved_in_finish(sample, aligned):
     assert sorted(row200)[:2] == [3, 4]
     v = g.make_variant(sample=sample, link="remcas", splice="split_one")
     buf = torch.empty(n + 4, dtype=torch.int32, device="cuda")
-    lab = buf[:n] if aligned else buf[1:n + 1]                 # 4-byte offset: the multi-kernel pass
+    lab = buf[:n] if aligned else buf[1:n + 1]                 # 4-byte offset: the scalar gathering kernel
     for offs in (dev(off), dev(_u32(off))):
         fn = g.gconn_cc_csr32 if offs.dtype == torch.int32 else g.gconn_cc_csr
         fn(n, offs, dev(cols), lab, v)
@@ -148,7 +148,7 @@ def test_lmax_root_moved_in_finish(sample, aligned):
 
 @pytest.mark.parametrize("block", [128, 192])
 def test_other_finish_block_sizes(block):
-    """A finish block size other than the fused pass's takes the multi-kernel pass."""
+    """Finish kernels with another block size give the same labels."""
     v = g.make_variant(sample="kout", link="remcas", splice="split_one", block=block)
     for name, n, e in GRAPHS:
         off, cols = CSR[name]

@@ -98,7 +98,7 @@ def test_profiled_plan_records_kernels():
         g.gconn_sync()
         g.gconn_profile_sync()
     prof = g.gconn_profile_get()
-    assert prof["kout"][0] == 3 and prof["tail"][0] == 3     # gathering, finish, finalisation: one launch
+    assert prof["kout"][0] == 3 and prof["finalize"][0] == 3
     assert all(ms > 0 for _, ms in prof.values())          # the captured pairs really time each replay
     assert g.gconn_launch_count() - c0 == 3 * sum(1 for _ in prof) or g.gconn_launch_count() > c0
     assert (host_u32(lab) == oracle.cc_uf(n, e)).all()
