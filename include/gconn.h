@@ -282,8 +282,13 @@ gconn_status gconn_inc_destroy(gconn_inc* h);
  * launch, and runs different sessions' launches concurrently.  Per session a
  * query sees exactly the inserts submitted before it: a run of inserts, or of
  * queries, starts only after the session's previous run finished.
- * Requests use HOST buffers, which must stay valid until gconn_server_wait
- * returns for that ticket; answers are written to `result` (uint8 per pair).
+ * Requests use host (or device) buffers, which must stay valid until
+ * gconn_server_wait returns for that ticket; answers are written to `result`
+ * (uint8 per pair).  Where the device can use a request's buffers in place
+ * (device memory; page-locked host memory; pageable host memory on a device
+ * with coherent access to it) the kernels read the pairs and write the
+ * answers there directly and such requests merge without a size limit;
+ * otherwise they are staged through pinned buffers of cfg.slot_pairs pairs.
  * gconn_server_wait blocks until the request completed and gives its latency
  * (submit to answer available, host clock); each ticket is waited for once
  * (a second wait, or a ticket never issued, returns E_INVAL).  All calls are

@@ -11,6 +11,12 @@
 // overlap the next one's staging.  Admission is bounded by a device-memory
 // budget and by the number of steps in flight.
 //
+// Where the kernels can use a request's buffers in place (device memory, or
+// host memory the device reads directly: page-locked, or pageable on a device
+// with coherent access), the step reads its pairs and writes its answers
+// there: no staging copy, no copies to and from the device, and no size limit
+// on the step (only the segment table is copied).
+//
 // Exactness per session: requests form phases of consecutive inserts or
 // consecutive queries; a session joins a step only with requests of the phase
 // it already has in flight (or any phase when it has nothing in flight), so a
@@ -53,6 +59,11 @@ struct Request {
     const uint32_t* pairs;        // host
     uint8_t* result;              // host, queries only
     Clock::time_point submitted;
+    // device-usable addresses of pairs / result when kernels can use the
+    // client's host buffers in place (host_direct), else null
+    const uint32_t* d_pairs;
+    uint8_t* d_result;
+    bool direct() const { return d_pairs && (op != GCONN_OP_QUERY || d_result); }
 };
 
 struct Session {
@@ -74,6 +85,8 @@ struct Seg {
     uint32_t* H;
     unsigned long long* W;
     uint32_t n, op, cap, seed;
+    const uint2* src;             // in-place steps: the request's pairs
+    uint8_t* dst;                 //                 and answers (client memory)
 };
 
 struct StepBuf {
@@ -88,6 +101,7 @@ struct StepBuf {
 struct Step {
     int buf = -1;
     bool solo = false;            // one request through its handle's own calls
+    bool direct = false;          // every request read / answered in place
     std::vector<Request> reqs;
     std::vector<uint32_t> seg_of; // request -> its answer offset (queries)
     uint64_t total = 0, answers = 0, bytes = 0;
@@ -95,8 +109,11 @@ struct Step {
     gconn_status status = GCONN_OK;
 };
 
-// Multi-forest union / query over one launch range of a merged step.
-template <int L, int F, int S>
+// Multi-forest union / query over one launch range of a merged step.  An
+// in-place step (DIRECT) reads each request's pairs and writes its answers in
+// the client's own buffers through the segment's addresses; a staged step
+// uses the step's packed device copy.
+template <int L, int F, int S, bool DIRECT>
 __global__ void __launch_bounds__(256) k_serve(const uint2* __restrict__ pairs, unsigned long long total,
                                                const Seg* __restrict__ segs, uint32_t nseg, uint8_t* out,
                                                uint32_t* err) {
@@ -117,7 +134,7 @@ __global__ void __launch_bounds__(256) k_serve(const uint2* __restrict__ pairs, 
         UFState s;
         s.P = g.P; s.H = g.H; s.W = g.W; s.sf = nullptr; s.err = err; s.Lk = nullptr;
         s.n = g.n; s.cap = g.cap; s.seed = g.seed;
-        uint2 e = __ldcs(pairs + i);
+        uint2 e = DIRECT ? __ldcs(g.src + (i - g.start)) : __ldcs(pairs + i);
         bool inrange = e.x < g.n && e.y < g.n;
         if (!inrange) atomicOr(err, GC_DERR_RANGE);
         Spin sp(g.cap);
@@ -130,7 +147,8 @@ __global__ void __launch_bounds__(256) k_serve(const uint2* __restrict__ pairs, 
                 else if (F == FD_NAIVE) a = same_root_lockstep(s, e.x, e.y, sp);
                 else a = uf_find<F, true>(s, e.x, sp) == uf_find<F, true>(s, e.y, sp);
             }
-            out[g.out + (i - g.start)] = a;
+            if (DIRECT) g.dst[i - g.start] = a;
+            else out[g.out + (i - g.start)] = a;
         }
     }
 }
@@ -208,6 +226,8 @@ gconn_status status_of_err(uint32_t e) {
 
 // A merged step: stage every request's pairs (grouped by union rule), copy
 // once, launch per rule, copy the answers back, all on the buffer's stream.
+// An in-place step copies only its segment table: the kernels read the
+// pairs and write the answers in the clients' buffers.
 gconn_status launch_merged(gconn_server* S, Step& sp, std::vector<Session*>& owners) {
     StepBuf& b = S->bufs[sp.buf];
     cudaStream_t st = b.st;
@@ -221,11 +241,13 @@ gconn_status launch_merged(gconn_server* S, Step& sp, std::vector<Session*>& own
     uint64_t pos = 0, ans = 0;
     for (size_t j = 0; j < idx.size(); ++j) {
         const Request& r = sp.reqs[idx[j]];
-        memcpy(b.h_pairs + 2 * pos, r.pairs, sizeof(uint32_t) * 2 * r.count);
+        if (!sp.direct) memcpy(b.h_pairs + 2 * pos, r.pairs, sizeof(uint32_t) * 2 * r.count);
         const IncView& v = owners[idx[j]]->view;
         Seg& g = b.h_segs[j];
         g.start = pos;
         g.out = ans;
+        g.src = (const uint2*)r.d_pairs;
+        g.dst = r.d_result;
         g.P = v.P; g.H = v.H; g.W = v.W;
         g.n = v.n;
         g.op = (uint32_t)r.op;
@@ -252,14 +274,19 @@ gconn_status launch_merged(gconn_server* S, Step& sp, std::vector<Session*>& own
     for (size_t r = 0; r < ranges.size(); ++r)
         for (size_t j = ranges[r].first; j < ranges[r].second; ++j) b.h_segs[j].start -= r0s[r];
     size_t seg_bytes = sizeof(Seg) * nseg;
-    // one device block: pairs | answers | segments | error word
-    size_t off_out = sizeof(uint32_t) * 2 * pos;
-    size_t off_seg = (off_out + ans + 255) & ~(size_t)255;
+    // one device block: pairs | answers | segments | error word (an
+    // in-place step keeps only the segments and the error word)
+    size_t off_out = sp.direct ? 0 : sizeof(uint32_t) * 2 * pos;
+    size_t off_seg = (off_out + (sp.direct ? 0 : ans) + 255) & ~(size_t)255;
     size_t off_err = off_seg + seg_bytes;
+    // from the library's caching pool: the step's block is reused, not mapped
+    // and unmapped per step
     char* d = nullptr;
-    GC_CUDA(cudaMallocAsync((void**)&d, off_err + 16, st));
+    cudaMemPool_t pool = scratch_pool();
+    GC_CUDA(pool ? cudaMallocFromPoolAsync((void**)&d, off_err + 16, pool, st)
+                 : cudaMallocAsync((void**)&d, off_err + 16, st));
     GC_CUDA(cudaMemsetAsync(d + off_err, 0, sizeof(uint32_t), st));
-    GC_CUDA(cudaMemcpyAsync(d, b.h_pairs, off_out, cudaMemcpyHostToDevice, st));
+    if (!sp.direct) GC_CUDA(cudaMemcpyAsync(d, b.h_pairs, off_out, cudaMemcpyHostToDevice, st));
     GC_CUDA(cudaMemcpyAsync(d + off_seg, b.h_segs, seg_bytes, cudaMemcpyHostToDevice, st));
     uint32_t* d_err = (uint32_t*)(d + off_err);
     const Seg* d_segs = (const Seg*)(d + off_seg);
@@ -269,13 +296,13 @@ gconn_status launch_merged(gconn_server* S, Step& sp, std::vector<Session*>& own
         uint64_t r0 = r0s[r], r1 = r + 1 < ranges.size() ? r0s[r + 1] : pos;
         const uint2* rp = (const uint2*)d + r0;
         GC_TRY(dispatch_rule(key[idx[a]], [&]<int l, int f, int k2>() {
-            auto k = k_serve<l, f, k2>;
+            auto k = sp.direct ? k_serve<l, f, k2, true> : k_serve<l, f, k2, false>;
             return launch("serve", k, grid_for(k, 256, r1 - r0), 256, 0, st, rp, (unsigned long long)(r1 - r0),
                           d_segs + a, (uint32_t)(c - a), d_out, d_err);
         }));
         S->launches++;
     }
-    if (ans) GC_CUDA(cudaMemcpyAsync(b.h_out, d + off_out, ans, cudaMemcpyDeviceToHost, st));
+    if (ans && !sp.direct) GC_CUDA(cudaMemcpyAsync(b.h_out, d + off_out, ans, cudaMemcpyDeviceToHost, st));
     GC_CUDA(cudaMemcpyAsync(b.h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     GC_CUDA(cudaFreeAsync(d, st));
     GC_CUDA(cudaEventRecord(sp.done, st));
@@ -297,6 +324,7 @@ gconn_status launch_solo(gconn_server* S, Step& sp, Session& ses) {
 void worker_loop(gconn_server* S) {
     cudaSetDevice(S->device);
     const uint64_t C = S->cfg.slot_pairs;
+    auto last_progress = Clock::now();
     std::unique_lock<std::mutex> lk(S->mu);
     while (true) {
         // 1. completions
@@ -312,7 +340,7 @@ void worker_loop(gconn_server* S) {
             if (q != cudaSuccess && sp.status == GCONN_OK) sp.status = cuda_status(q);
             if (!sp.solo && sp.status == GCONN_OK) {
                 sp.status = status_of_err(*b.h_err);
-                for (size_t i = 0; i < sp.reqs.size(); ++i) {
+                for (size_t i = 0; i < sp.reqs.size() && !sp.direct; ++i) {
                     const Request& r = sp.reqs[i];
                     if (r.op == GCONN_OP_QUERY) memcpy(r.result, b.h_out + sp.seg_of[i], r.count);
                 }
@@ -368,7 +396,7 @@ void worker_loop(gconn_server* S) {
                 if (ses.pending.empty()) continue;
                 const Request& r = ses.pending.front();
                 if (ses.inflight_phase != -1 && ses.inflight_phase != r.op) continue;
-                if (ses.mergeable && r.count <= C) continue;
+                if (ses.mergeable && (r.count <= C || r.direct())) continue;
                 uint64_t need = (sizeof(uint32_t) * 2 + (r.op == GCONN_OP_QUERY ? 1 : 0)) * r.count;
                 if (S->bytes_inflight && S->bytes_inflight + need > S->cfg.device_budget_bytes) break;
                 int bi = free_buf();
@@ -394,6 +422,7 @@ void worker_loop(gconn_server* S) {
             std::vector<Session*> owners;
             auto it = S->sessions.begin();
             std::advance(it, S->rr % ns);
+            int kind = -1;                  // in-place (1) or staged (0): fixed by the first request taken
             for (size_t visited = 0; visited < ns; ++visited, ++it) {
                 if (it == S->sessions.end()) it = S->sessions.begin();
                 Session& ses = it->second;
@@ -402,11 +431,16 @@ void worker_loop(gconn_server* S) {
                 if (ses.inflight_phase != -1 && ses.inflight_phase != op) continue;
                 while (!ses.pending.empty() && ses.pending.front().op == op && sp->reqs.size() < MAX_SEGS) {
                     const Request& r = ses.pending.front();
-                    if (r.count > C || sp->total + r.count > C) break;
-                    uint64_t need = (sizeof(uint32_t) * 2 + (op == GCONN_OP_QUERY ? 1 : 0)) * r.count;
+                    int rk = r.direct() ? 1 : 0;
+                    if (kind != -1 && rk != kind) break;
+                    // an in-place step needs no staging: no size limit, no device budget
+                    if (!rk && (r.count > C || sp->total + r.count > C)) break;
+                    uint64_t need = rk ? 0 : (sizeof(uint32_t) * 2 + (op == GCONN_OP_QUERY ? 1 : 0)) * r.count;
                     if (S->bytes_inflight + sp->bytes + need > S->cfg.device_budget_bytes &&
                         !(S->bytes_inflight == 0 && sp->reqs.empty()))
                         break;
+                    kind = rk;
+                    sp->direct = rk == 1;
                     sp->reqs.push_back(r);
                     owners.push_back(&ses);
                     sp->total += r.count;
@@ -415,7 +449,7 @@ void worker_loop(gconn_server* S) {
                     ses.inflight_phase = op;
                     ses.inflight += 1;
                 }
-                if (sp->total >= C || sp->reqs.size() >= MAX_SEGS) break;
+                if ((kind == 0 && sp->total >= C) || sp->reqs.size() >= MAX_SEGS) break;
             }
             if (!sp->reqs.empty()) start_step(std::move(sp), owners);
         }
@@ -425,11 +459,17 @@ void worker_loop(gconn_server* S) {
             for (auto& kv : S->sessions) any |= !kv.second.pending.empty();
             if (!any) break;
         }
+        if (launched || progressed) last_progress = Clock::now();
         if (!launched && !progressed) {
             if (S->inflight.empty()) S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
             else {
+                // steps in flight: poll their events by yielding for the first
+                // 200 us after the last progress (a timed sleep overshoots by
+                // tens of microseconds, which a short step would wait for),
+                // then by short sleeps
                 lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(5));
+                if (Clock::now() - last_progress < std::chrono::microseconds(200)) std::this_thread::yield();
+                else std::this_thread::sleep_for(std::chrono::microseconds(20));
                 lk.lock();
             }
         }
@@ -512,10 +552,15 @@ extern "C" gconn_status gconn_server_submit(gconn_server* S, uint32_t session, i
     if (!S || !ticket || (op != GCONN_OP_INSERT && op != GCONN_OP_QUERY)) return GCONN_E_INVAL;
     if ((count && !pairs) || count > GC_MAX_COUNT) return GCONN_E_INVAL;
     if (op == GCONN_OP_QUERY && count && !result) return GCONN_E_INVAL;
+    // where the kernels can use the client's buffers in place (device memory,
+    // or host memory the device reads directly), a step skips its staging
+    auto usable = [](const void* p) -> const void* { return !p ? nullptr : is_device_ptr(p) ? p : host_direct(p); };
+    const uint32_t* d_pairs = (const uint32_t*)usable(pairs);
+    uint8_t* d_result = op == GCONN_OP_QUERY ? (uint8_t*)usable(result) : nullptr;
     std::lock_guard<std::mutex> lk(S->mu);
     auto it = S->sessions.find(session);
     if (it == S->sessions.end() || it->second.closing) return GCONN_E_INVAL;
-    Request r{S->next_ticket++, session, op, count, pairs, result, Clock::now()};
+    Request r{S->next_ticket++, session, op, count, pairs, result, Clock::now(), d_pairs, d_result};
     *ticket = r.ticket;
     S->unclaimed.insert(r.ticket);
     if (count == 0) {

@@ -17,14 +17,14 @@ def test_parallel_rmat_stream_equals_serial():
 
 def test_serving_trace_shape():
     total = 50_000
-    n, trace = bench.serving_trace(2, 12, total, 99)
+    n, trace, answers = bench.serving_trace(2, 12, total, 99)
     assert n == 1 << 12 and len(trace) == 2
     for s, reqs in enumerate(trace):
-        ops = [op for op, _ in reqs]
+        ops = [op for op, _, _ in reqs]
         assert ops == [0, 1] * (len(reqs) // 2)
-        sizes = [len(a) for _, a in reqs[::2]]
-        assert sizes == [len(a) for _, a in reqs[1::2]] == bench.inc_batches(99 + s, total)
+        sizes = [len(a) for _, a, _ in reqs[::2]]
+        assert sizes == [len(a) for _, a, _ in reqs[1::2]] == bench.inc_batches(99 + s, total)
         assert sum(sizes) == total
         assert all(s_ >= 1000 for s_ in sizes[:-1])
-        ins = np.concatenate([a for op, a in reqs if op == 0])
+        ins = np.concatenate([a for op, a, _ in reqs if op == 0])
         assert np.array_equal(ins, bench.rmat_stream(12, total, 99 + s, graphgen.permutation(1 << 12, 99, 6)))
