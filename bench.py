@@ -135,13 +135,14 @@ def make_static_input(rank: int, scale: int = SCALE, m: int = M_EDGES):
     return n, e, off, cols, seed
 
 
-def inc_batches(seed: int, total: int = INC_TOTAL):
-    """Insert-batch sizes floor(10^(3+5U)) until `total` (last one truncated)."""
-    h = graphgen.hash_fill(seed, 11, 0, 4096)
+def inc_batches(seed: int, total: int = INC_TOTAL, lo: float = 3.0, hi: float = 8.0):
+    """Insert-batch sizes floor(10^(lo+(hi-lo)U)) (default: log-uniform in
+    [10^3, 10^8]) until `total` (last one truncated)."""
+    h = graphgen.hash_fill(seed, 11, 0, 1 << 20)
     sizes, tot = [], 0
     for x in h:
         u = (int(x) >> 11) * 2.0 ** -53
-        b = int(10 ** (3 + 5 * u))
+        b = int(10 ** (lo + (hi - lo) * u))
         b = min(b, total - tot)
         sizes.append(b)
         tot += b
@@ -451,7 +452,12 @@ def run_ours(args, rank, world, local_rank):
         result["spanning_forest"] = run_forest(g, torch, dev, stream, args, n, M, d_off32, d_cols, labels, flush, st,
                                                *roof_args)
     if rank == 0 and not args.no_serving:
-        result["serving"] = run_serving(g, torch, args)
+        loads = [float(x) for x in args.serve_loads.split(",")]
+        # the incremental workload's scale: 2^28 ops per session, batches of 10^3 - 10^8
+        result["serving"] = run_serving(g, torch, args, args.serve_sessions, args.serve_ops, INC_N_SCALE,
+                                        (3.0, 8.0), loads)
+        # many sessions, small requests (10^3 - 10^4): where merging launches pays
+        result["serving_small_requests"] = run_serving(g, torch, args, 32, 1 << 20, 20, (3.0, 4.0), loads)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(n, e, args.cpu_seconds)
         result["cpu_multicore"] = cpu_multicore(n, M, off, cols, args.scale)
@@ -809,7 +815,7 @@ def host_array(shape, dtype, pinned):
     return torch.empty(shape, dtype=tdt, pin_memory=True).numpy().view(dtype)
 
 
-def serving_trace(sessions, n_scale, total, seed, pinned=False):
+def serving_trace(sessions, n_scale, total, seed, pinned=False, law=(3.0, 8.0)):
     """Per session s: its own RMAT scale-24 insert stream (seed + s) and as
     many uniform query pairs, cut into insert batches of log-uniform size in
     [10^3, 10^8] (the incremental workload's law), each followed by a query
@@ -824,7 +830,7 @@ def serving_trace(sessions, n_scale, total, seed, pinned=False):
         qry = graphgen.pairs_range(n, 0, total, seed + s, out=host_array((total, 2), np.uint32, pinned))
         answers.append(host_array(total, np.uint8, pinned))
         reqs, a = [], 0
-        for b in inc_batches(seed + s, total):
+        for b in inc_batches(seed + s, total, *law):
             reqs.append((0, ins[a:a + b], a))
             reqs.append((1, qry[a:a + b], a))
             a += b
@@ -832,7 +838,7 @@ def serving_trace(sessions, n_scale, total, seed, pinned=False):
     return n, out, answers
 
 
-def run_serving(g, torch, args):
+def run_serving(g, torch, args, sessions, ops, n_scale, law, loads):
     """Continuous batching at the incremental workload's scale, open loop.
     S sessions (n = 2^24 each, Union-Early), each with its own stream of 2^28
     RMAT insertions and 2^28 query pairs in batches of log-uniform size in
@@ -844,8 +850,8 @@ def run_serving(g, torch, args):
     gconn_server, which admits them as slots and staging memory free up and
     overlaps different sessions' work.  Latency is arrival to answer on the
     host clock; every query answer must be identical."""
-    S = args.serve_sessions
-    n, trace, answers = serving_trace(S, INC_N_SCALE, args.serve_ops, SEED_SERVE, pinned=True)
+    S = sessions
+    n, trace, answers = serving_trace(S, n_scale, ops, SEED_SERVE, pinned=True, law=law)
     v = g.make_variant(link="early")
     total_ops = sum(len(a) for reqs in trace for _, a, _ in reqs)
     nreq = sum(len(r) for r in trace)
@@ -881,44 +887,45 @@ def run_serving(g, torch, args):
         return lat, span
 
     def served_run(arrivals):
+        """One submitter thread (all sessions, arrival order) and one thread
+        that waits for the tickets in submission order; latency comes from
+        the server's own clock (submit to answer) plus the submitter's lag."""
         srv = g.gconn_server_create()
         sids = [g.gconn_server_open_session(srv, n, v) for _ in range(S)]
-        lat = [[] for _ in range(S)]
-        done = [0.0] * S
-        tickets = [[] for _ in range(S)]
+        order = sorted((arrivals[s][r], s, r) for s in range(S) for r in range(len(trace[s])))
+        tickets, lat = [], []
         cv = threading.Condition()
         t0 = time.perf_counter()
 
-        def submitter(s):
-            for r, (op, a, _) in enumerate(trace[s]):
-                at = arrivals[s][r]
+        def submitter():
+            for at, s, r in order:
                 now = time.perf_counter() - t0
                 if at > now:
                     time.sleep(at - now)
+                op, a, _ = trace[s][r]
                 lag = (time.perf_counter() - t0 - at) * 1e3
                 t = g.gconn_server_submit(srv, sids[s], g.GCONN_OP_INSERT if op == 0 else g.GCONN_OP_QUERY,
                                           len(a), a, out_of(s, r) if op == 1 else None)
                 with cv:
-                    tickets[s].append((t, lag))
+                    tickets.append((t, lag))
                     cv.notify_all()
 
-        def waiter(s):
-            for r in range(len(trace[s])):
+        def waiter():
+            for i in range(len(order)):
                 with cv:
-                    cv.wait_for(lambda: len(tickets[s]) > r)
-                    t, lag = tickets[s][r]
-                lat[s].append(g.gconn_server_wait(srv, t) + lag)
-            done[s] = time.perf_counter() - t0
+                    cv.wait_for(lambda: len(tickets) > i)
+                    t, lag = tickets[i]
+                lat.append(g.gconn_server_wait(srv, t) + lag)
 
-        th = [threading.Thread(target=f, args=(s,)) for s in range(S) for f in (submitter, waiter)]
+        th = [threading.Thread(target=submitter), threading.Thread(target=waiter)]
         for t in th:
             t.start()
         for t in th:
             t.join()
+        span = time.perf_counter() - t0 - order[0][0]
         st = g.gconn_server_stats(srv)
         g.gconn_server_destroy(srv)
-        span = max(done) - min(arrivals[s][0] for s in range(S))
-        return [x for l in lat for x in l], span, st
+        return lat, span, st
 
     # the plain loop back to back: its answers are the reference and its
     # capacity sets the offered loads
@@ -927,7 +934,7 @@ def run_serving(g, torch, args):
     cap_ops = total_ops / span0
     rng = np.random.default_rng(SEED_SERVE)
     rows, identical = [], True
-    for frac in [float(x) for x in args.serve_loads.split(",")]:
+    for frac in loads:
         rate = frac * cap_ops                                   # offered ops/s, all sessions
         arrivals = []
         for s in range(S):                                      # Poisson, mean request size per session
@@ -951,7 +958,7 @@ def run_serving(g, torch, args):
                                 "groups": st["groups"]},
                      "identical_answers": same})
     return {"sessions": S, "n_per_session": n, "requests": nreq, "ops": total_ops,
-            "ops_per_session": args.serve_ops, "batch_law": "log-uniform sizes in [1e3, 1e8], insert then query",
+            "ops_per_session": ops, "batch_law": f"log-uniform sizes in [1e{law[0]:g}, 1e{law[1]:g}], insert then query",
             "plain_capacity_ops_per_s": cap_ops, "loads": rows, "identical_answers": identical,
             "arrivals": "open loop: seeded Poisson per session at the offered load",
             "latency": "host clock, arrival to answers in the client's buffer",
@@ -1074,14 +1081,20 @@ SWEEP_LINKS = ([("async", f, "none") for f in ["naive", "compress", "split", "ha
 
 
 def run_sweep(args):
-    """Config-2 sweep: sampling x linking x compression on the RMAT s22 CSR;
-    every variant's labels are compared bit for bit with the oracle's."""
+    """Sampling x linking x compression on a CSR graph (the RMAT scale-22
+    workload, or with --sweep-graph grid_paths the high-diameter one); every
+    variant's labels are compared bit for bit with the oracle's."""
     import torch
     import oracle
     import paper_2008_11839_gb300 as g
     g.build()
     dev = torch.device("cuda", 0)
-    n, e, off, cols, seed = make_static_input(0)
+    if args.sweep_graph == "grid_paths":
+        n, e = graphgen.grid_paths(4096, 0.05, 64, 1 << 18, 0x6C0A0003)
+        off, cols = graphgen.csr(n, e)
+    else:
+        n, e, off, cols, seed = make_static_input(0)
+    m_und = len(e)
     ref = oracle.cc_uf(n, e)
     d_off = torch.from_numpy(off.view(np.int64)).to(dev)
     d_cols = torch.from_numpy(cols.view(np.int32)).to(dev)
@@ -1093,6 +1106,12 @@ def run_sweep(args):
     for sample in samples:
         for link, f, sp in SWEEP_LINKS:
             spec = f"{sample}/{link}/{f}/{sp}"
+            if args.sweep_graph == "grid_paths" and sample == "none" and link in ("lp", "stergiou"):
+                # label propagation needs about as many rounds as the paths are long (2^18):
+                # beyond the round cap
+                rows.append({"variant": spec, "skipped": "rounds ~ path length (2^18) exceed the round cap"})
+                print(json.dumps(rows[-1]), flush=True)
+                continue
             v = parse_variant(g, spec)
             plan = None
             try:
@@ -1122,8 +1141,8 @@ def run_sweep(args):
                     ts.append(a.elapsed_time(b))
                 g.gconn_sync(stream)
                 ms = float(np.median(ts))
-                row = {"variant": spec, "ms": round(ms, 4), "edges_per_s": M_EDGES / (ms * 1e-3), "exact": exact,
-                       "input_equivalent_gbs": round((8 * M_EDGES + 12 * n) / (ms * 1e-3) / 1e9, 1),
+                row = {"variant": spec, "ms": round(ms, 4), "edges_per_s": m_und / (ms * 1e-3), "exact": exact,
+                       "input_equivalent_gbs": round((8 * m_und + 12 * n) / (ms * 1e-3) / 1e9, 1),
                        "launch": "captured plan" if plan is not None else "direct calls"}
             except g.GconnError as ex:
                 row = {"variant": spec, "error": str(ex)}
@@ -1132,6 +1151,7 @@ def run_sweep(args):
             rows.append(row)
             print(json.dumps(row), flush=True)
     ok = [r for r in rows if "ms" in r]
+    rows = [r for r in rows if "skipped" not in r]
     ok.sort(key=lambda r: r["ms"])
     print(json.dumps({"sweep_best": ok[:10], "all_exact": all(r["exact"] for r in ok), "variants": len(rows)}))
 
@@ -1379,6 +1399,7 @@ def main():
     ap.add_argument("--ablation-variants", default="kout/remcas/naive/split_one,kout/early/naive/none,"
                                                    "hb/remcas/naive/split_one")
     ap.add_argument("--sweep-samples", default="none,kout,hb,bfs")
+    ap.add_argument("--sweep-graph", choices=["rmat", "grid_paths"], default="rmat")
     ap.add_argument("--sweep-steps", type=int, default=5)
     ap.add_argument("--stats", action="store_true", help="sampling Cov / IC / Time %% per sampling method")
     ap.add_argument("--ratio-sweep", action="store_true", help="mixed batches at several insert:query ratios")

@@ -22,8 +22,15 @@
  * - Edge, pair and query counts (m, b, q, count) are at most 2^60
  *   (E_INVAL above), so every byte size fits in 64 bits.
  * - Every pointer may be device memory or host memory (pageable or pinned);
- *   the library checks each one.  Host inputs are copied to the device; host
- *   outputs are filled before the call returns.  The caller owns every buffer
+ *   the library checks each one.  A host input that a call reads once or
+ *   only in part (CSR columns; COO edges and insert / query batches for the
+ *   union-find finishes) is read in place by the kernels when the device can
+ *   address it: page-locked memory, or pageable memory on a device with
+ *   coherent access to it (cudaDevAttrPageableMemoryAccess, e.g. over
+ *   NVLink-C2C); other host inputs are copied to the device, as are all of
+ *   them when the environment sets GCONN_HOST_STAGE=1.  Host inputs must not
+ *   change while the call runs.  Host outputs are filled before the call
+ *   returns.  The caller owns every buffer
  *   it passes; the library never frees caller memory.  Temporary device
  *   memory comes from the device's stream-ordered pool (cudaMallocAsync) and
  *   is returned on the same stream.
@@ -287,8 +294,10 @@ gconn_status gconn_inc_destroy(gconn_inc* h);
  * (uint8 per pair).  Where the device can use a request's buffers in place
  * (device memory; page-locked host memory; pageable host memory on a device
  * with coherent access to it) the kernels read the pairs and write the
- * answers there directly and such requests merge without a size limit;
- * otherwise they are staged through pinned buffers of cfg.slot_pairs pairs.
+ * answers there directly; otherwise they are staged through pinned buffers of
+ * cfg.slot_pairs pairs.  A merged launch holds at most cfg.slot_pairs pairs:
+ * a larger request runs alone (a small request merged with it would wait for
+ * it).
  * gconn_server_wait blocks until the request completed and gives its latency
  * (submit to answer available, host clock); each ticket is waited for once
  * (a second wait, or a ticket never issued, returns E_INVAL).  All calls are

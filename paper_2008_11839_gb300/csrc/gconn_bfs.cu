@@ -119,7 +119,7 @@ __device__ void bfs_pick_source(const OffT* off, uint32_t n, uint64_t seed, BfsC
 }
 
 template <class OffT>
-__global__ void __launch_bounds__(BFS_BLOCK, 6) k_bfs(const OffT* __restrict__ off, const uint32_t* __restrict__ cols,
+__global__ void __launch_bounds__(BFS_BLOCK, 8) k_bfs(const OffT* __restrict__ off, const uint32_t* __restrict__ cols,
                                                    uint32_t n, uint64_t seed, uint32_t* dist, uint32_t* qa,
                                                    uint32_t* qb, BfsCtl* c, uint32_t* P, u64w* W, uint32_t* sf,
                                                    uint32_t* lmax, uint32_t* err) {

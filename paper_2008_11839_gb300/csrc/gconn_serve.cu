@@ -14,8 +14,9 @@
 // Where the kernels can use a request's buffers in place (device memory, or
 // host memory the device reads directly: page-locked, or pageable on a device
 // with coherent access), the step reads its pairs and writes its answers
-// there: no staging copy, no copies to and from the device, and no size limit
-// on the step (only the segment table is copied).
+// there: no staging copy and no copies to and from the device (only the
+// segment table is copied); such a request above a step's size runs as a
+// step of its own instead of through its handle's calls.
 //
 // Exactness per session: requests form phases of consecutive inserts or
 // consecutive queries; a session joins a step only with requests of the phase
@@ -433,8 +434,14 @@ void worker_loop(gconn_server* S) {
                     const Request& r = ses.pending.front();
                     int rk = r.direct() ? 1 : 0;
                     if (kind != -1 && rk != kind) break;
-                    // an in-place step needs no staging: no size limit, no device budget
-                    if (!rk && (r.count > C || sp->total + r.count > C)) break;
+                    // a step's requests all finish together, so a large request
+                    // merges with nothing (a small one would wait for it): an
+                    // in-place request above C pairs runs as a step of its own,
+                    // other steps stop at C pairs (a staged request above C is a
+                    // solo step, 2a)
+                    if (rk && r.count > C && !sp->reqs.empty()) break;
+                    if (!rk && r.count > C) break;
+                    if (sp->total && sp->total + r.count > C) break;
                     uint64_t need = rk ? 0 : (sizeof(uint32_t) * 2 + (op == GCONN_OP_QUERY ? 1 : 0)) * r.count;
                     if (S->bytes_inflight + sp->bytes + need > S->cfg.device_budget_bytes &&
                         !(S->bytes_inflight == 0 && sp->reqs.empty()))
@@ -449,7 +456,7 @@ void worker_loop(gconn_server* S) {
                     ses.inflight_phase = op;
                     ses.inflight += 1;
                 }
-                if ((kind == 0 && sp->total >= C) || sp->reqs.size() >= MAX_SEGS) break;
+                if (sp->total >= C || sp->reqs.size() >= MAX_SEGS) break;
             }
             if (!sp->reqs.empty()) start_step(std::move(sp), owners);
         }
