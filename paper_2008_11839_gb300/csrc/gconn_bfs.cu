@@ -25,7 +25,7 @@ constexpr int BFS_BLOCK = 256;
 constexpr uint64_t BEAMER_ALPHA = 14;   // top-down -> bottom-up when m_f > m_u / alpha
 constexpr uint64_t BEAMER_BETA = 24;    // bottom-up -> top-down when n_f < n / beta
 
-struct BfsSlot {
+struct alignas(128) BfsSlot {    // a line per slot: appends to one do not slow reads of another
     uint32_t qlen;                 // frontier length
     uint32_t pad;
     unsigned long long degsum;     // arcs out of the frontier
@@ -38,21 +38,61 @@ struct BfsCtl {
     BfsSlot slot[3];
 };
 
-__device__ __forceinline__ void warp_append(bool has, uint32_t val, uint64_t deg, uint32_t* q, BfsSlot* c) {
+// Top-down claims of one level, staged per block in shared memory: a warp
+// reserves its claims with a shared atomic, and the block reserves space on
+// the queue once, at the end of the level (stage_flush).  A high-diameter
+// graph runs thousands of levels with small frontiers, where one reservation
+// per warp on the same two counters costs more than the level's own work.
+constexpr uint32_t BFS_STAGE = 1024;
+struct BfsStage {
+    uint32_t cnt;                  // claims staged (may pass BFS_STAGE: the rest went to the queue)
+    uint32_t base;                 // the block's reservation on the queue
+    unsigned long long deg;        // arcs out of the staged and overflowed claims
+    uint32_t q[BFS_STAGE];
+};
+
+__device__ __forceinline__ void warp_stage(bool has, uint32_t val, uint64_t deg, uint32_t* q, BfsSlot* c,
+                                           BfsStage& sg) {
     unsigned m = __ballot_sync(0xFFFFFFFFu, has);
     if (!m) return;
-    unsigned lane = threadIdx.x & 31u;
-    unsigned leader = __ffs(m) - 1;
+    const unsigned lane = threadIdx.x & 31u, leader = __ffs(m) - 1;
     unsigned long long dsum = has ? deg : 0;
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xFFFFFFFFu, dsum, o);
-    dsum = __shfl_sync(0xFFFFFFFFu, dsum, 0);
-    uint32_t base = 0;
+    if (lane == 0 && dsum) atomicAdd(&sg.deg, dsum);
+    const uint32_t cnt = __popc(m);
+    uint32_t base = 0, gbase = 0;
     if (lane == leader) {
-        base = atomicAdd(&c->qlen, (uint32_t)__popc(m));
-        atomicAdd(&c->degsum, dsum);
+        base = atomicAdd(&sg.cnt, cnt);
+        uint32_t room = base < BFS_STAGE ? BFS_STAGE - base : 0;
+        if (cnt > room) gbase = atomicAdd(&c->qlen, cnt - room);   // what does not fit goes to the queue now
     }
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (has) q[base + __popc(m & ((1u << lane) - 1))] = val;
+    gbase = __shfl_sync(0xFFFFFFFFu, gbase, leader);
+    const uint32_t room = base < BFS_STAGE ? BFS_STAGE - base : 0;
+    const uint32_t rank = __popc(m & ((1u << lane) - 1));
+    if (has) {
+        if (rank < room) sg.q[base + rank] = val;
+        else q[gbase + rank - room] = val;
+    }
+}
+
+// Every thread of the block, at the end of a top-down level: one reservation
+// for the staged claims, copied out coalesced; the staged degree sum is added
+// once.  The counters are reset for the next level, which starts after a
+// grid barrier (a block synchronisation).
+__device__ __forceinline__ void stage_flush(uint32_t* q, BfsSlot* c, BfsStage& sg) {
+    __syncthreads();
+    const uint32_t k = sg.cnt < BFS_STAGE ? sg.cnt : BFS_STAGE;
+    if (threadIdx.x == 0) {
+        if (k) sg.base = atomicAdd(&c->qlen, k);
+        if (sg.deg) atomicAdd(&c->degsum, sg.deg);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) q[sg.base + i] = sg.q[i];
+    if (threadIdx.x == 0) {
+        sg.cnt = 0;
+        sg.deg = 0;
+    }
 }
 
 // Block-wide append (every thread of the block calling): one reservation on
@@ -127,6 +167,13 @@ __global__ void __launch_bounds__(BFS_BLOCK, 8) k_bfs(const OffT* __restrict__ o
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gw = tid / 32, nw = stride / 32;
     const unsigned lane = threadIdx.x & 31u;
+    __shared__ BfsStage sg;
+    __shared__ uint32_t s_flen;
+    __shared__ unsigned long long s_mf;
+    if (threadIdx.x == 0) {
+        sg.cnt = 0;
+        sg.deg = 0;
+    }
     for (uint64_t v = tid; v < n; v += stride) dist[v] = GC_DINF;
     if (!grid_sync(&c->bar, err)) return;
     if (blockIdx.x == 0) bfs_pick_source(off, n, seed, c, dist, qa);
@@ -139,8 +186,13 @@ __global__ void __launch_bounds__(BFS_BLOCK, 8) k_bfs(const OffT* __restrict__ o
     for (uint32_t level = 0;; ++level) {
         BfsSlot* cur = &c->slot[level % 3];
         BfsSlot* nxt = &c->slot[(level + 1) % 3];
-        const uint32_t flen = __ldcg(&cur->qlen);
-        const uint64_t mf = __ldcg(&cur->degsum);
+        if (threadIdx.x == 0) {            // one read of the level's counters per block
+            s_flen = __ldcg(&cur->qlen);
+            s_mf = __ldcg(&cur->degsum);
+        }
+        __syncthreads();
+        const uint32_t flen = s_flen;
+        const uint64_t mf = s_mf;
         if (flen == 0) break;
         if (level > n) {
             if (tid == 0) atomicOr(err, GC_DERR_NONCONV);
@@ -174,9 +226,10 @@ __global__ void __launch_bounds__(BFS_BLOCK, 8) k_bfs(const OffT* __restrict__ o
                             dy = (uint64_t)off[y + 1] - (uint64_t)off[y];
                         }
                     }
-                    warp_append(claimed, y, dy, nq, nxt);
+                    warp_stage(claimed, y, dy, nq, nxt, sg);
                 }
             }
+            stage_flush(nq, nxt, sg);
         } else {                           // every unvisited vertex looks for a parent in the frontier
             const uint64_t rounds = ((uint64_t)n + stride - 1) / stride;
             for (uint64_t r = 0; r < rounds; ++r) {     // uniform trip count for the block-wide append

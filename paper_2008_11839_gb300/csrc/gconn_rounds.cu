@@ -41,10 +41,20 @@ struct RoundCtl {
 __device__ __forceinline__ uint64_t gtid() { return (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ uint64_t gstride() { return (uint64_t)gridDim.x * blockDim.x; }
 
-// Records that round r changed something (one atomic per warp); called by
+// Records that round r changed something (one atomic per block); called by
 // every thread of a block at the same point.
 __device__ __forceinline__ void mark_changed(bool ch, uint32_t* chg, uint32_t r) {
-    if (__any_sync(0xFFFFFFFFu, ch) && (threadIdx.x & 31u) == 0) atomicMax(chg, r + 1);
+    if (__syncthreads_or(ch) && threadIdx.x == 0) atomicMax(chg, r + 1);
+}
+
+// Whether round r changed anything, read after the round's last barrier:
+// thread 0 reads the word once for the block.  The next round reaches
+// another barrier (which synchronises the block) before it reads again.
+__device__ __forceinline__ bool round_changed(const RoundCtl* ctl, uint32_t r) {
+    __shared__ uint32_t s_chg;
+    if (threadIdx.x == 0) s_chg = __ldcg(&ctl->chg);
+    __syncthreads();
+    return s_chg >= r + 1;
 }
 
 __device__ __forceinline__ uint64_t edge_count(uint64_t m_host, const unsigned long long* m_dev) {
@@ -136,7 +146,7 @@ __global__ void __launch_bounds__(RB) k_sv(const uint2* __restrict__ E, const ui
         }
         compress_copy(n, P, prev, err);
         if (!grid_sync(&ctl->bar, err)) return;
-        if (__ldcg(&ctl->chg) < r + 1) {   // no change in round r (chg only grows)
+        if (!round_changed(ctl, r)) {   // no change in round r (chg only grows)
             finish_rounds(ctl, r + 1);
             return;
         }
@@ -233,7 +243,7 @@ __global__ void __launch_bounds__(RB) k_lt(const uint2* __restrict__ E_in, uint2
             mark_changed(ch, &ctl->chg, r);
             if (!grid_sync(&ctl->bar, err)) return;
         }
-        if (__ldcg(&ctl->chg) < r + 1) {   // no change in round r (chg only grows)
+        if (!round_changed(ctl, r)) {   // no change in round r (chg only grows)
             finish_rounds(ctl, r + 1);
             break;
         }
@@ -264,7 +274,7 @@ __global__ void __launch_bounds__(RB) k_lp(const uint2* __restrict__ E, uint64_t
         }
         mark_changed(ch, &ctl->chg, r);
         if (!grid_sync(&ctl->bar, err)) return;
-        if (__ldcg(&ctl->chg) < r + 1) {   // no change in round r (chg only grows)
+        if (!round_changed(ctl, r)) {   // no change in round r (chg only grows)
             finish_rounds(ctl, r + 1);
             break;
         }
@@ -307,7 +317,7 @@ __global__ void __launch_bounds__(RB) k_stergiou(const uint2* __restrict__ E, ui
         }
         mark_changed(ch, &ctl->chg, r);
         if (!grid_sync(&ctl->bar, err)) return;
-        if (__ldcg(&ctl->chg) < r + 1) {   // no change in round r (chg only grows)
+        if (!round_changed(ctl, r)) {   // no change in round r (chg only grows)
             finish_rounds(ctl, r + 1);
             break;
         }

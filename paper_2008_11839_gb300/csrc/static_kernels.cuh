@@ -997,14 +997,21 @@ static __global__ void k_finalize_gathered(UFState s, const uint32_t* lmax_p, co
 
 // ------------------------------------------------------------ grid barrier
 // A barrier over every block of a cooperative launch (all blocks resident).
-// Two words, zero-initialised: arrivals and a generation.  Thread 0 of each
-// block reads the generation, then arrives; the last arrival resets the count
-// and advances the generation; the others wait for it to change.  The wait is
-// bounded: it ends when the device error word shows that a block gave up, or
-// after GRID_WAIT_NS, when it raises that error itself -- then every block
-// returns instead of waiting forever.
+// Arrivals are counted in two levels so they do not serialise on one word:
+// block b arrives at group b % G (G <= GRID_GROUPS counters); the last
+// arrival of a group arrives at the top counter, and the last of those resets
+// the count and advances the generation, which the other blocks' thread 0
+// poll for.  Every word has a 128-byte line of its own, so the polling does
+// not slow the arrivals.  Every word starts at zero and returns to zero after
+// each barrier, except the generation.  The wait is bounded: it ends when the
+// device error word shows that a block gave up, or after GRID_WAIT_NS, when it
+// raises that error itself -- then every block returns instead of waiting
+// forever.
+constexpr int GRID_GROUPS = 32;
 struct GridBar {
-    uint32_t count, gen;
+    uint32_t gen, pad0[31];
+    uint32_t count, pad1[31];
+    uint32_t group[GRID_GROUPS][32];
 };
 constexpr unsigned long long GRID_WAIT_NS = 20ull * 1000000000ull;
 
@@ -1027,10 +1034,21 @@ static __device__ __noinline__ bool grid_sync(GridBar* b, uint32_t* err) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int good = 1;
+        const uint32_t nb = gridDim.x;
+        const uint32_t G = nb < GRID_GROUPS ? nb : GRID_GROUPS;
+        const uint32_t grp = blockIdx.x % G;
+        const uint32_t gsize = nb / G + (grp < nb % G ? 1u : 0u);
         uint32_t g = ld_acquire_gpu(&b->gen);
         __threadfence();                     // this block's writes before its arrival
-        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+        bool last = false;
+        if (atomicAdd(&b->group[grp][0], 1u) == gsize - 1) {
+            atomicExch(&b->group[grp][0], 0u);
+            __threadfence();                 // the group's writes before the top arrival
+            last = atomicAdd(&b->count, 1u) == G - 1;
+        }
+        if (last) {
             atomicExch(&b->count, 0u);
+            __threadfence();                 // every arrival seen before the release
             st_release_gpu(&b->gen, g + 1);
         } else {
             unsigned long long t0 = globaltimer_ns();
@@ -1043,7 +1061,7 @@ static __device__ __noinline__ bool grid_sync(GridBar* b, uint32_t* err) {
                     break;
                 }
                 __nanosleep(ns);
-                if (ns < 256) ns *= 2;
+                if (ns < 128) ns *= 2;
             }
         }
         __threadfence();
