@@ -1106,7 +1106,7 @@ def run_sweep(args):
     for sample in samples:
         for link, f, sp in SWEEP_LINKS:
             spec = f"{sample}/{link}/{f}/{sp}"
-            if args.sweep_graph == "grid_paths" and sample == "none" and link in ("lp", "stergiou"):
+            if args.sweep_graph == "grid_paths" and sample == "none" and link == "lp":
                 # label propagation needs about as many rounds as the paths are long (2^18):
                 # beyond the round cap
                 rows.append({"variant": spec, "skipped": "rounds ~ path length (2^18) exceed the round cap"})

@@ -124,8 +124,21 @@ gconn_status read_and_clear_err(cudaStream_t st) {
     return GCONN_OK;
 }
 
+// A host thread that has not used CUDA yet has no current context, and the
+// pointer queries below then cannot see the device's mappings (a page-locked
+// buffer would be staged instead of read in place): bind the current
+// device's primary context to the thread first, once per thread.
+static void bind_context() {
+    static thread_local bool bound = false;
+    if (bound) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaSetDevice(dev) != cudaSuccess) cudaGetLastError();
+    bound = true;
+}
+
 bool is_device_ptr(const void* p) {
     if (!p) return false;
+    bind_context();
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
@@ -157,6 +170,7 @@ const void* host_direct(const void* p) {
         return e && e[0] == '1';
     }();
     if (!p || staged) return nullptr;
+    bind_context();
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
