@@ -79,6 +79,40 @@ def test_csr_spanning_forest(sample, combo):
         assert (host_u32(lab) == REF[name]).all(), name
 
 
+def _hub_bipartite(seed=11):
+    """K(64, 4096) with every 7th edge listed twice, vertex ids permuted.  The
+    BFS source is one of the 64 vertices of degree ~4,700 (all 1,024 seeded
+    samples missing them has probability ~1e-7), and its top-down first level
+    claims 4,096 vertices in one warp: more than a block stages in shared
+    memory, in chunks of fewer than 32 claims where a duplicate falls, so the
+    staging list overflows part way through a warp's reservation."""
+    a, b = 64, 4096
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(a + b).astype(np.uint32)
+    ai, bi = np.meshgrid(np.arange(a), np.arange(a, a + b), indexing="ij")
+    e = np.stack([ai.ravel(), bi.ravel()], 1)
+    e = np.concatenate([e, e[::7]])
+    rng.shuffle(e)
+    return a + b, perm[e].astype(np.uint32)
+
+
+@pytest.mark.parametrize("combo", UF_FOREST, ids=combo_id)
+def test_bfs_staged_claims_overflow(combo):
+    link, f, sp = combo
+    n, e = _hub_bipartite()
+    # plus an isolated edge and isolated vertices: the BFS reaches one component
+    e = np.concatenate([e, np.array([[n, n + 1]], np.uint32)])
+    n += 5
+    ref = oracle.cc_uf(n, e)
+    off, cols = graphgen.csr(n, e)
+    v = g.make_variant(sample="bfs", link=link, find=f, splice=sp)
+    assert (_cc_csr(n, off, cols, v) == ref).all()
+    ids, lab = g.spanning_forest_csr(n, dev(off), dev(cols), v, labels=True)
+    g.gconn_sync()
+    assert oracle.sf_check_arcs(n, off, cols, ids.cpu().numpy().astype(np.uint64), ref) == 0
+    assert (host_u32(lab) == ref).all()
+
+
 @pytest.mark.parametrize("sample", ["none", "kout"])
 def test_shiloach_vishkin(sample):
     v = g.make_variant(sample=sample, link="sv")
