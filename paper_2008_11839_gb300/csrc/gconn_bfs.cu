@@ -44,6 +44,7 @@ struct BfsCtl {
 // graph runs thousands of levels with small frontiers, where one reservation
 // per warp on the same two counters costs more than the level's own work.
 constexpr uint32_t BFS_STAGE = 1024;
+constexpr uint32_t BFS_PROBE_MIN = 16384;   // frontier size from which claims probe first
 struct BfsStage {
     uint32_t cnt;                  // claims staged (may pass BFS_STAGE: the rest went to the queue)
     uint32_t base;                 // the block's reservation on the queue
@@ -207,6 +208,10 @@ __global__ void __launch_bounds__(BFS_BLOCK, 8) k_bfs(const OffT* __restrict__ o
             clr->degsum = 0;
         }
         if (topdown) {                     // one warp per frontier vertex claims unvisited neighbours
+            // a large frontier reads a neighbour's distance before trying to
+            // claim it (most are taken: a load is cheaper than a failed CAS);
+            // a small one, latency-bound, goes straight to the CAS
+            const bool probe = flen >= BFS_PROBE_MIN;
             for (uint64_t i = gw; i < flen; i += nw) {
                 uint32_t u = __ldcg(q + i);
                 uint64_t lo = off[u], hi = off[u + 1];
@@ -219,11 +224,15 @@ __global__ void __launch_bounds__(BFS_BLOCK, 8) k_bfs(const OffT* __restrict__ o
                         y = cols[a];
                         if (y >= n) {
                             atomicOr(err, GC_DERR_RANGE);
-                        } else if (__ldcg(dist + y) == GC_DINF &&
-                                   atomicCAS(dist + y, GC_DINF, level + 1) == GC_DINF) {
-                            claimed = true;
-                            if (sf) sf[y] = (uint32_t)a;
-                            dy = (uint64_t)off[y + 1] - (uint64_t)off[y];
+                        } else {
+                            // y's degree is loaded with the claim, not after it
+                            const uint64_t ylo = off[y], yhi = off[y + 1];
+                            if ((!probe || __ldcg(dist + y) == GC_DINF) &&
+                                atomicCAS(dist + y, GC_DINF, level + 1) == GC_DINF) {
+                                claimed = true;
+                                if (sf) sf[y] = (uint32_t)a;
+                                dy = yhi - ylo;
+                            }
                         }
                     }
                     warp_stage(claimed, y, dy, nq, nxt, sg);

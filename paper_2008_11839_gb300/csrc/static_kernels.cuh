@@ -999,19 +999,22 @@ static __global__ void k_finalize_gathered(UFState s, const uint32_t* lmax_p, co
 // A barrier over every block of a cooperative launch (all blocks resident).
 // Arrivals are counted in two levels so they do not serialise on one word:
 // block b arrives at group b % G (G <= GRID_GROUPS counters); the last
-// arrival of a group arrives at the top counter, and the last of those resets
-// the count and advances the generation, which the other blocks' thread 0
-// poll for.  Every word has a 128-byte line of its own, so the polling does
-// not slow the arrivals.  Every word starts at zero and returns to zero after
-// each barrier, except the generation.  The wait is bounded: it ends when the
-// device error word shows that a block gave up, or after GRID_WAIT_NS, when it
-// raises that error itself -- then every block returns instead of waiting
-// forever.
+// arrival of a group arrives at the top counter, and the last of those
+// publishes the generation that the other blocks' thread 0 poll for.  The
+// counters only grow (64-bit, zeroed before the launch): a block's own
+// arrival count tells it which barrier it is at, so no word is reset and no
+// block reads the generation before arriving.  The arrivals are acquire-
+// release atomics and the publication a release store, so the writes of
+// every block before the barrier are visible to every block after it.  Every
+// word has a 128-byte line of its own, so the polling does not slow the
+// arrivals.  The wait is bounded: it ends when the device error word shows
+// that a block gave up, or after GRID_WAIT_NS, when it raises that error
+// itself -- then every block returns instead of waiting forever.
 constexpr int GRID_GROUPS = 32;
 struct GridBar {
     uint32_t gen, pad0[31];
-    uint32_t count, pad1[31];
-    uint32_t group[GRID_GROUPS][32];
+    unsigned long long top, pad1[15];
+    unsigned long long group[GRID_GROUPS][16];
 };
 constexpr unsigned long long GRID_WAIT_NS = 20ull * 1000000000ull;
 
@@ -1028,6 +1031,11 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
 __device__ __forceinline__ void st_release_gpu(uint32_t* p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_gpu(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
 
 static __device__ __noinline__ bool grid_sync(GridBar* b, uint32_t* err) {
     __shared__ int ok;
@@ -1038,22 +1046,20 @@ static __device__ __noinline__ bool grid_sync(GridBar* b, uint32_t* err) {
         const uint32_t G = nb < GRID_GROUPS ? nb : GRID_GROUPS;
         const uint32_t grp = blockIdx.x % G;
         const uint32_t gsize = nb / G + (grp < nb % G ? 1u : 0u);
-        uint32_t g = ld_acquire_gpu(&b->gen);
-        __threadfence();                     // this block's writes before its arrival
+        // releases this block's writes (ordered before by the block barrier)
+        const unsigned long long old = atom_add_acq_rel_gpu(&b->group[grp][0], 1ull);
+        const uint32_t target = (uint32_t)(old / gsize) + 1u;   // the generation this barrier publishes
         bool last = false;
-        if (atomicAdd(&b->group[grp][0], 1u) == gsize - 1) {
-            atomicExch(&b->group[grp][0], 0u);
-            __threadfence();                 // the group's writes before the top arrival
-            last = atomicAdd(&b->count, 1u) == G - 1;
+        if (old % gsize == gsize - 1) {     // the group's last arrival: acquires the group, releases it on
+            const unsigned long long top = atom_add_acq_rel_gpu(&b->top, 1ull);
+            last = top % G == G - 1;
         }
         if (last) {
-            atomicExch(&b->count, 0u);
-            __threadfence();                 // every arrival seen before the release
-            st_release_gpu(&b->gen, g + 1);
+            st_release_gpu(&b->gen, target);
         } else {
             unsigned long long t0 = globaltimer_ns();
             unsigned ns = 32;
-            while (ld_acquire_gpu(&b->gen) == g) {
+            while ((int32_t)(ld_acquire_gpu(&b->gen) - target) < 0) {
                 if (__ldcg(err) & GC_DERR_NONCONV) { good = 0; break; }
                 if (globaltimer_ns() - t0 > GRID_WAIT_NS) {
                     atomicOr(err, GC_DERR_NONCONV);
@@ -1064,7 +1070,6 @@ static __device__ __noinline__ bool grid_sync(GridBar* b, uint32_t* err) {
                 if (ns < 128) ns *= 2;
             }
         }
-        __threadfence();
         ok = good;
     }
     __syncthreads();
