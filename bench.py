@@ -440,6 +440,8 @@ def run_ours(args, rank, world, local_rank):
 
     legs = {"rmat_s22": (n, e, lab_timed)}      # final labels, checked against the oracle below
     roof_args = (hbm, peak_src)
+    if rank == 0 and not args.no_coo:
+        result["static_cc_coo"] = run_c2_coo(g, torch, dev, stream, args, flush, n, e, lab_timed, *roof_args)
     if rank == 0 and not args.no_c1:
         result["static_cc_er_c1"], legs["er_c1"] = run_c1(g, torch, dev, stream, args, flush, *roof_args)
     if rank == 0 and not args.no_c3:
@@ -497,6 +499,38 @@ def _pass_runner(g, plan_fn, direct_fn):
     if plan is not None:
         return plan, (lambda st: g.gconn_plan_run(plan, st)), "captured plan"
     return None, direct_fn, "direct calls"
+
+
+C2_COO_VARIANTS = ["none/remcas/naive/split_one", "none/async/halve/none", "none/early/naive/none"]
+
+
+def run_c2_coo(g, torch, dev, stream, args, flush, n, e, lab_ref, hbm, peak_src):
+    """The same RMAT graph as the headline pass, as its COO list without
+    sampling (the plain method: init, one union per edge, finalisation), one
+    captured plan per variant; the roofline on 8m + 12n bytes.  Labels must
+    equal the headline pass's (which the CPU-baseline leg compares with the
+    oracle)."""
+    m = len(e)
+    d_e = torch.from_numpy(e.view(np.int32)).to(dev)
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    ref = torch.from_numpy(lab_ref.view(np.int32)).to(dev)
+    rows = []
+    for spec in C2_COO_VARIANTS:
+        v = parse_variant(g, spec)
+        plan, run, how = _pass_runner(g, lambda: g.gconn_plan_create_cc(n, m, d_e, lab, v),
+                                      lambda st: g.gconn_cc(n, m, d_e, lab, v, st))
+        ts = _time_passes(torch, stream, lambda: run(stream), flush, 2, max(3, min(args.steps, 5)), 5000)
+        g.gconn_sync(stream)
+        if plan is not None:
+            g.gconn_plan_destroy(plan)
+        ms = float(np.mean(ts))
+        rows.append({"variant": spec, "launch": how, "ms": round(ms, 4), "edges_per_s": m / (ms * 1e-3),
+                     "roofline": roofline(8 * m + 12 * n, ms, hbm, peak_src, bytes_model="8m + 12n"),
+                     "labels_equal_csr_pass": bool(torch.equal(lab, ref))})
+    del d_e, lab, ref
+    torch.cuda.empty_cache()
+    return {"workload": f"static_cc_rmat_s{args.scale}_coo", "n": n, "m_undirected": m,
+            "input": "COO (uint32 pairs), resident, no sampling", "l2": "flushed between passes", "rows": rows}
 
 
 def run_c1(g, torch, dev, stream, args, flush, hbm, peak_src):
@@ -1388,6 +1422,7 @@ def main():
     ap.add_argument("--serve-loads", default="0.3,0.6,0.9,1.2",
                     help="offered loads as fractions of the plain loop's back-to-back throughput")
     ap.add_argument("--no-c1", action="store_true", help="skip the ER n=65,536 COO leg")
+    ap.add_argument("--no-coo", action="store_true", help="skip the headline graph's COO no-sampling rows")
     ap.add_argument("--no-c3", action="store_true", help="skip the grid + paths leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-edges", type=int, default=M_EDGES)
