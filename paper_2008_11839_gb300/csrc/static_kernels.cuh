@@ -510,6 +510,20 @@ static __global__ void k_w_from_p(uint32_t n, const uint32_t* P, u64w* W) {
 }
 
 
+// Vertex v's nch warp tasks from slot `base` of the task array (reserved by
+// the caller).  Slots at or above task_cap do not exist: a vertex whose tasks
+// do not all fit goes to the overflow list instead, and the slots it reserved
+// below the cap get empty tasks (a chunk index past every row's end), since
+// the readers take every slot below min(count, cap) as a task.
+__device__ __forceinline__ void put_tasks(uint64_t v, uint64_t nch, uint64_t base, unsigned long long* tasks,
+                                          uint32_t task_cap, uint32_t* over, uint32_t* nover) {
+    const bool fits = base + nch <= task_cap;
+    const unsigned long long tag = (unsigned long long)v << 32;
+    for (uint64_t j = 0; j < nch && base + j < task_cap; ++j)
+        tasks[base + j] = tag | (fits ? j : 0xFFFFFFFFull);
+    if (!fits) over[atomicAdd(nover, 1u)] = (uint32_t)v;
+}
+
 // Vertex gathering (the VG optimisation): vertices whose sampled label is not
 // L_max and that have edges become active.  Low-degree ones go to a list
 // (thread per vertex); higher-degree ones are cut into TASK_ARCS-arc warp
@@ -560,11 +574,7 @@ static __global__ void __launch_bounds__(256) k_vg(const OffT* __restrict__ off,
         if (act && !is_small) {
             uint64_t nch = (deg + TASK_ARCS - 1) / TASK_ARCS;
             uint32_t base = atomicAdd(ntasks, (uint32_t)nch);
-            if ((uint64_t)base + nch <= task_cap) {
-                for (uint64_t j = 0; j < nch; ++j) tasks[base + j] = ((unsigned long long)v << 32) | j;
-            } else {
-                over[atomicAdd(nover, 1u)] = (uint32_t)v;
-            }
+            put_tasks(v, nch, base, tasks, task_cap, over, nover);
         }
     }
 }
@@ -675,19 +685,30 @@ __device__ __forceinline__ void vg4_pass(const OffT* __restrict__ off, const UFS
             uint32_t base = 0;
             if (lane == 31 && total) base = atomicAdd(nsmall, total);
             base = __shfl_sync(0xFFFFFFFFu, base, 31) + (inc - c);
+            // the warp's higher-degree vertices reserve their tasks together:
+            // one atomic per warp, not one per vertex (without sampling most
+            // of a graph's vertices are here)
+            uint32_t tc = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (((nib & ~snib) >> j) & 1u) tc += (uint32_t)((o[j + 1] - o[j] + TASK_ARCS - 1) / TASK_ARCS);
+            uint32_t tinc = tc;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                uint32_t t = __shfl_up_sync(0xFFFFFFFFu, tinc, d);
+                if ((int)lane >= d) tinc += t;
+            }
+            const uint32_t ttotal = __shfl_sync(0xFFFFFFFFu, tinc, 31);
+            uint32_t tbase = 0;
+            if (lane == 31 && ttotal) tbase = atomicAdd(ntasks, ttotal);
+            uint64_t tb = (uint64_t)__shfl_sync(0xFFFFFFFFu, tbase, 31) + (tinc - tc);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if ((snib >> j) & 1u) small[base++] = (uint32_t)(v0 + j);
                 if (((nib & ~snib) >> j) & 1u) {
-                    uint64_t deg = o[j + 1] - o[j];
-                    uint64_t nch = (deg + TASK_ARCS - 1) / TASK_ARCS;
-                    uint32_t tb = atomicAdd(ntasks, (uint32_t)nch);
-                    if ((uint64_t)tb + nch <= task_cap) {
-                        for (uint64_t t = 0; t < nch; ++t)
-                            tasks[tb + t] = ((unsigned long long)(v0 + j) << 32) | t;
-                    } else {
-                        over[atomicAdd(nover, 1u)] = (uint32_t)(v0 + j);
-                    }
+                    uint64_t nch = (o[j + 1] - o[j] + TASK_ARCS - 1) / TASK_ARCS;
+                    put_tasks(v0 + j, nch, tb, tasks, task_cap, over, nover);
+                    tb += nch;
                 }
             }
         }

@@ -113,6 +113,45 @@ def test_bfs_staged_claims_overflow(combo):
     assert (host_u32(lab) == ref).all()
 
 
+def _dense_graph():
+    """Two cliques of 1,200 vertices (~1.44 M edges) plus a path, ids permuted:
+    without sampling every vertex is active with 1,199 arcs (5 tasks of 256
+    arcs), ~12,000 tasks against a task array of n + 1,024 slots, so the
+    reservations run past the cap part way through some vertex's tasks."""
+    rng = np.random.default_rng(21)
+    k = 1200
+    iu, ju = np.triu_indices(k, 1)
+    e = np.concatenate([np.stack([iu, ju], 1), np.stack([iu + k, ju + k], 1),
+                        np.stack([np.arange(2 * k, 2 * k + 99), np.arange(2 * k + 1, 2 * k + 100)], 1)])
+    n = 2 * k + 100 + 7                         # and seven isolated vertices
+    perm = rng.permutation(n).astype(np.uint32)
+    e = perm[e].astype(np.uint32)
+    rng.shuffle(e)
+    return n, e
+
+
+@pytest.mark.parametrize("spec", ["none/remcas/naive/split_one", "none/async/halve/none", "none/sv/naive/none",
+                                  "none/lt/PRS/none", "hb/remcas/naive/split_one"])
+def test_task_array_overflow(spec):
+    n, e = _dense_graph()
+    ref = oracle.cc_uf(n, e)
+    off, cols = graphgen.csr(n, e)
+    p = spec.split("/")
+    kw = dict(sample=p[0], link=p[1])
+    if p[1] == "lt":
+        kw["lt"] = p[2]
+    else:
+        kw["find"], kw["splice"] = p[2], p[3]
+    v = g.make_variant(**kw)
+    for _ in range(2):                          # the second run reuses the first run's scratch
+        assert (_cc_csr(n, off, cols, v) == ref).all(), spec
+    if p[1] in ("remcas", "sv"):
+        ids, lab = g.spanning_forest_csr(n, dev(off), dev(cols), v, labels=True)
+        g.gconn_sync()
+        assert oracle.sf_check_arcs(n, off, cols, ids.cpu().numpy().astype(np.uint64), ref) == 0
+        assert (host_u32(lab) == ref).all()
+
+
 @pytest.mark.parametrize("sample", ["none", "kout"])
 def test_shiloach_vishkin(sample):
     v = g.make_variant(sample=sample, link="sv")
