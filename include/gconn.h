@@ -360,8 +360,8 @@ gconn_status gconn_plan_destroy(gconn_plan* p);
  * sampling on COO input).  Graph g has vertices [vtx_off[g], vtx_off[g+1])
  * and edges [edge_off[g], edge_off[g+1]) of the concatenated arrays; its
  * edges use LOCAL ids in [0, n_g) and its labels are LOCAL min ids.
- * Graphs with n_g <= class_max_n[last] run entirely in shared memory (16-bit
- * parents, one CTA per graph, one persistent kernel per size class on its own
+ * Graphs with n_g <= class_max_n[last] run entirely in shared memory (32-bit
+ * parents up to n_g = 58,112, 16-bit above, one CTA per graph, one persistent kernel per size class on its own
  * stream); larger graphs use the global-memory path one launch each.
  *   vtx_off, edge_off : uint64[G+1] (device or host; read on the host once)
  *   edges             : uint32[2 * edge_off[G]] pairs, DEVICE memory

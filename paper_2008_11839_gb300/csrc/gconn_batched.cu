@@ -1,9 +1,10 @@
 // gconn_batched.cu -- many independent graphs in one persistent launch.
 //
 // Each graph of the batch is one task for one CTA: its whole union-find lives
-// in shared memory as 16-bit parents (a graph of up to 65,536 vertices needs
-// at most 128 KiB), its edges stream once from HBM, and its labels are written
-// once.  Graphs are grouped into size classes; every class runs one
+// in shared memory, as 32-bit parents where the class's largest graph fits a
+// CTA's 227 KiB that way (n <= 58,112), else as 16-bit parents (a graph of up
+// to 65,536 vertices needs at most 128 KiB); its edges stream once from HBM,
+// and its labels are written once.  Graphs are grouped into size classes; every class runs one
 // persistent kernel (CTAs pull graphs from an atomic queue, largest first) on
 // its own forked stream, so the classes share the GPU, and the whole sequence
 // is captured into one CUDA graph at plan creation.  Block size and union rule
@@ -32,13 +33,17 @@ constexpr uint32_t SMEM_CAP = 1u << 20;   // loop cap per shared-memory union
 enum { BR_ASYNC_NAIVE = 0, BR_ASYNC_HALVE = 1, BR_REM_SPLIT = 2 };
 constexpr int BATCH_ILP = 8;   // edge loads in flight per thread
 
-__device__ __forceinline__ uint32_t sm_ld(const volatile uint16_t* P, uint32_t i) { return P[i]; }
+template <class T>
+__device__ __forceinline__ uint32_t sm_ld(const volatile T* P, uint32_t i) { return P[i]; }
 __device__ __forceinline__ uint32_t sm_cas(volatile uint16_t* P, uint32_t i, uint32_t cmp, uint32_t val) {
     return atomicCAS((unsigned short*)(P + i), (unsigned short)cmp, (unsigned short)val);
 }
+__device__ __forceinline__ uint32_t sm_cas(volatile uint32_t* P, uint32_t i, uint32_t cmp, uint32_t val) {
+    return atomicCAS((unsigned int*)(P + i), cmp, val);
+}
 
-template <int R>
-__device__ __forceinline__ uint32_t sm_find(volatile uint16_t* P, uint32_t u, uint32_t& left) {
+template <int R, class T>
+__device__ __forceinline__ uint32_t sm_find(volatile T* P, uint32_t u, uint32_t& left) {
     if constexpr (R == BR_ASYNC_HALVE) {
         while (left) {
             uint32_t v = sm_ld(P, u), w = sm_ld(P, v);
@@ -61,8 +66,8 @@ __device__ __forceinline__ uint32_t sm_find(volatile uint16_t* P, uint32_t u, ui
 
 // One union in shared memory: Union-Async (naive or halving find) or
 // Union-Rem-CAS with SplitAtomicOne (Algorithms 7, 11).
-template <int R>
-__device__ __forceinline__ void sm_union(volatile uint16_t* P, uint32_t u, uint32_t v, uint32_t* err) {
+template <int R, class T>
+__device__ __forceinline__ void sm_union(volatile T* P, uint32_t u, uint32_t v, uint32_t* err) {
     uint32_t left = SMEM_CAP;
     if (R == BR_REM_SPLIT) {
         uint32_t ru = u, rv = v;
@@ -81,13 +86,13 @@ __device__ __forceinline__ void sm_union(volatile uint16_t* P, uint32_t u, uint3
         atomicOr(err, GC_DERR_NONCONV);
         return;
     }
-    uint32_t pu = sm_find<R>(P, u, left), pv = sm_find<R>(P, v, left);
+    uint32_t pu = sm_find<R, T>(P, u, left), pv = sm_find<R, T>(P, v, left);
     while (pu != pv && left) {
         if (pu < pv) { uint32_t t = pu; pu = pv; pv = t; }
         if (sm_ld(P, pu) == pu && sm_cas(P, pu, pu, pv) == pu) return;
         --left;
-        pu = sm_find<R>(P, pu, left);
-        pv = sm_find<R>(P, pv, left);
+        pu = sm_find<R, T>(P, pu, left);
+        pv = sm_find<R, T>(P, pv, left);
     }
     if (!left) atomicOr(err, GC_DERR_NONCONV);
 }
@@ -95,12 +100,12 @@ __device__ __forceinline__ void sm_union(volatile uint16_t* P, uint32_t u, uint3
 // Persistent class kernel: CTAs pull graph indices (largest first) from an
 // atomic queue; each graph: init parents in shared memory, stream its edges,
 // union, then write every vertex's root (its min-id label) to global memory.
-template <int R>
+template <int R, class T>
 __global__ void k_batch_smem(const uint64_t* __restrict__ vo, const uint64_t* __restrict__ eo,
                              const uint2* __restrict__ E, uint32_t* __restrict__ labels,
                              const uint32_t* __restrict__ order, uint32_t count, uint32_t* queue, uint32_t* err) {
-    extern __shared__ uint16_t Psm_raw[];
-    volatile uint16_t* P = Psm_raw;
+    extern __shared__ uint32_t Psm_raw[];
+    volatile T* P = reinterpret_cast<volatile T*>(Psm_raw);
     __shared__ uint32_t s_idx;
     while (true) {
         if (threadIdx.x == 0) s_idx = atomicAdd(queue, 1u);
@@ -111,14 +116,14 @@ __global__ void k_batch_smem(const uint64_t* __restrict__ vo, const uint64_t* __
         uint64_t vb = vo[g];
         uint32_t n = (uint32_t)(vo[g + 1] - vb);
         uint64_t eb = eo[g], m = eo[g + 1] - eb;
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) P[i] = (uint16_t)i;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) P[i] = (T)i;
         __syncthreads();
         // BATCH_ILP coalesced edge loads in flight per thread before their
         // unions: the edge stream, not the shared-memory unions, is the
         // latency that bounds a large graph's CTA
         auto one = [&](uint2 e) {
             if (e.x >= n || e.y >= n) atomicOr(err, GC_DERR_RANGE);
-            else if (e.x != e.y) sm_union<R>(P, e.x, e.y, err);
+            else if (e.x != e.y) sm_union<R, T>(P, e.x, e.y, err);
         };
         const uint64_t B = blockDim.x;
         uint64_t j = threadIdx.x;
@@ -179,20 +184,28 @@ static int rule_of(int link, int find) {
     return find == GCONN_FIND_HALVE ? BR_ASYNC_HALVE : BR_ASYNC_NAIVE;
 }
 
-static void* smem_kernel(int rule) {
-    if (rule == BR_REM_SPLIT) return (void*)k_batch_smem<BR_REM_SPLIT>;
-    if (rule == BR_ASYNC_HALVE) return (void*)k_batch_smem<BR_ASYNC_HALVE>;
-    return (void*)k_batch_smem<BR_ASYNC_NAIVE>;
+static void* smem_kernel(int rule, bool wide) {
+    if (wide) {
+        if (rule == BR_REM_SPLIT) return (void*)k_batch_smem<BR_REM_SPLIT, uint32_t>;
+        if (rule == BR_ASYNC_HALVE) return (void*)k_batch_smem<BR_ASYNC_HALVE, uint32_t>;
+        return (void*)k_batch_smem<BR_ASYNC_NAIVE, uint32_t>;
+    }
+    if (rule == BR_REM_SPLIT) return (void*)k_batch_smem<BR_REM_SPLIT, uint16_t>;
+    if (rule == BR_ASYNC_HALVE) return (void*)k_batch_smem<BR_ASYNC_HALVE, uint16_t>;
+    return (void*)k_batch_smem<BR_ASYNC_NAIVE, uint16_t>;
 }
 
 // Launch one class's persistent kernel on stream st.
 static gconn_status launch_class(gconn_batch* b, int c, int block, int rule, cudaStream_t st) {
     uint32_t cnt = b->cls_begin[c + 1] - b->cls_begin[c];
     if (!cnt) return GCONN_OK;
-    size_t smem = sizeof(uint16_t) * (size_t)((b->cls_maxn[c] + 1) & ~1u);
+    // 32-bit parents where a CTA's shared memory holds them (no 16-bit CAS)
+    const bool wide = 4ull * b->cls_maxn[c] <= 227ull * 1024;
+    size_t smem = wide ? sizeof(uint32_t) * (size_t)b->cls_maxn[c]
+                       : sizeof(uint16_t) * (size_t)((b->cls_maxn[c] + 1) & ~1u);
     if (smem < 16) smem = 16;
     int per_sm = 0;
-    void* kf = smem_kernel(rule);
+    void* kf = smem_kernel(rule, wide);
     GC_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, block, smem));
     if (per_sm < 1) return GCONN_E_UNSUPPORTED;
@@ -201,14 +214,17 @@ static gconn_status launch_class(gconn_batch* b, int c, int block, int rule, cud
     uint32_t* q = b->queues + c;
     uint32_t* err = err_word();
     const uint2* E = (const uint2*)b->edges;
-    if (rule == BR_REM_SPLIT)
-        return launch("batch_smem", k_batch_smem<BR_REM_SPLIT>, grid, block, smem, st, b->vo, b->eo, E, b->labels, ord,
-                      cnt, q, err);
-    if (rule == BR_ASYNC_HALVE)
-        return launch("batch_smem", k_batch_smem<BR_ASYNC_HALVE>, grid, block, smem, st, b->vo, b->eo, E, b->labels,
-                      ord, cnt, q, err);
-    return launch("batch_smem", k_batch_smem<BR_ASYNC_NAIVE>, grid, block, smem, st, b->vo, b->eo, E, b->labels, ord,
-                  cnt, q, err);
+#define GC_BLAUNCH(RR, TT) \
+    return launch("batch_smem", k_batch_smem<RR, TT>, grid, block, smem, st, b->vo, b->eo, E, b->labels, ord, cnt, q, err)
+    if (wide) {
+        if (rule == BR_REM_SPLIT) GC_BLAUNCH(BR_REM_SPLIT, uint32_t);
+        if (rule == BR_ASYNC_HALVE) GC_BLAUNCH(BR_ASYNC_HALVE, uint32_t);
+        GC_BLAUNCH(BR_ASYNC_NAIVE, uint32_t);
+    }
+    if (rule == BR_REM_SPLIT) GC_BLAUNCH(BR_REM_SPLIT, uint16_t);
+    if (rule == BR_ASYNC_HALVE) GC_BLAUNCH(BR_ASYNC_HALVE, uint16_t);
+    GC_BLAUNCH(BR_ASYNC_NAIVE, uint16_t);
+#undef GC_BLAUNCH
 }
 
 // The whole batch on `st`: reset queues, fork one stream per class, join,
