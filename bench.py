@@ -457,7 +457,7 @@ def run_ours(args, rank, world, local_rank):
         loads = [float(x) for x in args.serve_loads.split(",")]
         # the incremental workload's scale: 2^28 ops per session, batches of 10^3 - 10^8
         result["serving"] = run_serving(g, torch, args, args.serve_sessions, args.serve_ops, INC_N_SCALE,
-                                        (3.0, 8.0), loads)
+                                        (3.0, 8.0), loads, args.serve_reps)
         # many sessions, small requests (10^3 - 10^4): where merging launches pays
         result["serving_small_requests"] = run_serving(g, torch, args, 32, 1 << 20, 20, (3.0, 4.0), loads)
     if rank == 0 and not args.no_cpu_baseline:
@@ -872,7 +872,7 @@ def serving_trace(sessions, n_scale, total, seed, pinned=False, law=(3.0, 8.0)):
     return n, out, answers
 
 
-def run_serving(g, torch, args, sessions, ops, n_scale, law, loads):
+def run_serving(g, torch, args, sessions, ops, n_scale, law, loads, reps=1):
     """Continuous batching at the incremental workload's scale, open loop.
     S sessions (n = 2^24 each, Union-Early), each with its own stream of 2^28
     RMAT insertions and 2^28 query pairs in batches of log-uniform size in
@@ -970,31 +970,41 @@ def run_serving(g, torch, args, sessions, ops, n_scale, law, loads):
     rows, identical = [], True
     for frac in loads:
         rate = frac * cap_ops                                   # offered ops/s, all sessions
-        arrivals = []
-        for s in range(S):                                      # Poisson, mean request size per session
-            mean_ops = sum(len(a) for _, a, _ in trace[s]) / len(trace[s])
-            gaps = rng.exponential(mean_ops * S / rate, len(trace[s]))
-            arrivals.append(list(np.cumsum(gaps)))
-        for buf in answers:
-            buf.fill(2)
-        pl, ps = plain_run(arrivals)
-        same_plain = same_as(ref)
-        for buf in answers:
-            buf.fill(2)
-        sl, ss, st = served_run(arrivals)
-        same = same_plain and same_as(ref)
+        # `reps` independent arrival draws over the same trace, latencies pooled
+        pl, sl, ps, ss, launches, groups, same, p50s = [], [], 0.0, 0.0, 0, 0, True, []
+        for _ in range(reps):
+            arrivals = []
+            for s in range(S):                                  # Poisson, mean request size per session
+                mean_ops = sum(len(a) for _, a, _ in trace[s]) / len(trace[s])
+                gaps = rng.exponential(mean_ops * S / rate, len(trace[s]))
+                arrivals.append(list(np.cumsum(gaps)))
+            for buf in answers:
+                buf.fill(2)
+            l1, s1 = plain_run(arrivals)
+            same &= same_as(ref)
+            for buf in answers:
+                buf.fill(2)
+            l2, s2, st = served_run(arrivals)
+            same &= same_as(ref)
+            pl += l1
+            sl += l2
+            ps += s1
+            ss += s2
+            launches += st["launches"]
+            groups += st["groups"]
+            p50s.append([round(pct(l1, 50), 3), round(pct(l2, 50), 3)])
         identical &= same
         rows.append({"offered_load_of_plain_capacity": frac, "offered_ops_per_s": rate,
-                     "plain": {"ops_per_s": total_ops / ps, "latency_ms_p50": round(pct(pl, 50), 3),
+                     "plain": {"ops_per_s": reps * total_ops / ps, "latency_ms_p50": round(pct(pl, 50), 3),
                                "latency_ms_p99": round(pct(pl, 99), 3)},
-                     "served": {"ops_per_s": total_ops / ss, "latency_ms_p50": round(pct(sl, 50), 3),
-                                "latency_ms_p99": round(pct(sl, 99), 3), "launches": st["launches"],
-                                "groups": st["groups"]},
-                     "identical_answers": same})
+                     "served": {"ops_per_s": reps * total_ops / ss, "latency_ms_p50": round(pct(sl, 50), 3),
+                                "latency_ms_p99": round(pct(sl, 99), 3), "launches": launches, "groups": groups},
+                     "p50_plain_served_per_draw": p50s, "identical_answers": same})
     return {"sessions": S, "n_per_session": n, "requests": nreq, "ops": total_ops,
             "ops_per_session": ops, "batch_law": f"log-uniform sizes in [1e{law[0]:g}, 1e{law[1]:g}], insert then query",
             "plain_capacity_ops_per_s": cap_ops, "loads": rows, "identical_answers": identical,
-            "arrivals": "open loop: seeded Poisson per session at the offered load",
+            "arrivals": f"open loop: seeded Poisson per session at the offered load; {reps} draws per load, "
+                        f"latencies pooled",
             "latency": "host clock, arrival to answers in the client's buffer",
             "inputs": "page-locked host memory (requests and answers)"}
 
@@ -1418,6 +1428,8 @@ def main():
                     help="time one insert and one query batch of this size after a 2^27-edge prefix")
     ap.add_argument("--inc-probe-variants", default="early/naive")
     ap.add_argument("--serve-sessions", type=int, default=2)
+    ap.add_argument("--serve-reps", type=int, default=5,
+                    help="arrival draws per offered load at the incremental workload's scale (latencies pooled)")
     ap.add_argument("--serve-ops", type=int, default=1 << 28, help="insertions (and queries) per serving session")
     ap.add_argument("--serve-loads", default="0.3,0.6,0.9,1.2",
                     help="offered loads as fractions of the plain loop's back-to-back throughput")
