@@ -10,7 +10,10 @@
 // graphs on exactly these per-level steps, Section 4.3) and the pass can be
 // captured into a CUDA graph.  Counters rotate through three slots: a level
 // reads slot L % 3, appends to slot (L + 1) % 3 and clears slot (L + 2) % 3,
-// which every block finished reading a level earlier.
+// which every block finished reading a level earlier.  On small frontiers of
+// low mean degree a level chains: a thread expands one of its own fresh
+// claims right away instead of queueing it (the sampling needs the reached
+// set, not exact levels), so such a level advances several hops.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -45,6 +48,12 @@ struct BfsCtl {
 // per warp on the same two counters costs more than the level's own work.
 constexpr uint32_t BFS_STAGE = 1024;
 constexpr uint32_t BFS_PROBE_MIN = 16384;   // frontier size from which claims probe first
+// Chained expansion on small, low-degree frontiers: a thread expands its
+// frontier vertex, then goes on to expand one of the vertices it just claimed
+// instead of queueing it, up to BFS_CHAIN_HOPS vertices per level.
+constexpr uint32_t BFS_CHAIN_MAX = 1u << 18;  // frontier size up to which levels chain
+constexpr uint64_t BFS_CHAIN_DEG = 8;         // ... when the frontier's mean degree is at most this
+constexpr uint32_t BFS_CHAIN_HOPS = 16;
 struct BfsStage {
     uint32_t cnt;                  // claims staged (may pass BFS_STAGE: the rest went to the queue)
     uint32_t base;                 // the block's reservation on the queue
@@ -75,6 +84,15 @@ __device__ __forceinline__ void warp_stage(bool has, uint32_t val, uint64_t deg,
         if (rank < room) sg.q[base + rank] = val;
         else q[gbase + rank - room] = val;
     }
+}
+
+// One thread's claim, staged in the block's shared list (a shared atomic;
+// what does not fit goes to the queue at once).
+__device__ __forceinline__ void thread_stage(uint32_t val, uint64_t deg, uint32_t* q, BfsSlot* c, BfsStage& sg) {
+    if (deg) atomicAdd(&sg.deg, (unsigned long long)deg);
+    const uint32_t p = atomicAdd(&sg.cnt, 1u);
+    if (p < BFS_STAGE) sg.q[p] = val;
+    else q[atomicAdd(&c->qlen, 1u)] = val;
 }
 
 // Every thread of the block, at the end of a top-down level: one reservation
@@ -207,7 +225,53 @@ __global__ void __launch_bounds__(BFS_BLOCK, 8) k_bfs(const OffT* __restrict__ o
             clr->qlen = 0;
             clr->degsum = 0;
         }
-        if (topdown) {                     // one warp per frontier vertex claims unvisited neighbours
+        if (topdown && flen <= BFS_CHAIN_MAX && mf <= BFS_CHAIN_DEG * (uint64_t)flen) {
+            // a thread per frontier vertex, chained: BFS sampling needs the
+            // reached set, not exact levels, so a vertex claimed here may be
+            // expanded at once (its neighbours are claimed with the same
+            // level mark); every claimed vertex is either expanded in the
+            // chain or queued, so the reached set is complete when the queue
+            // runs dry, and any claimed neighbour is a valid forest parent
+            for (uint64_t i = tid; i < flen; i += stride) {
+                uint32_t x = __ldcg(q + i);
+                for (uint32_t hop = 0; hop < BFS_CHAIN_HOPS; ++hop) {
+                    const uint64_t lo = off[x], hi = off[x + 1];
+                    uint32_t next = GC_DINF;
+                    for (uint64_t a0 = lo; a0 < hi; a0 += 4) {
+                        // four arcs at a time: their columns, then their
+                        // claims and degrees, each group of loads in flight together
+                        uint32_t y[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) y[k] = a0 + k < hi ? cols[a0 + k] : GC_DINF;
+                        uint32_t deg[4];
+                        bool got[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            got[k] = false;
+                            deg[k] = 0;
+                            if (y[k] == GC_DINF) continue;
+                            if (y[k] >= n) {
+                                atomicOr(err, GC_DERR_RANGE);
+                                continue;
+                            }
+                            const uint64_t dk = (uint64_t)off[y[k] + 1] - (uint64_t)off[y[k]];
+                            deg[k] = dk < 0xFFFFFFFFull ? (uint32_t)dk : 0xFFFFFFFFu;
+                            got[k] = atomicCAS(dist + y[k], GC_DINF, level + 1) == GC_DINF;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (!got[k]) continue;
+                            if (sf) sf[y[k]] = (uint32_t)(a0 + k);
+                            if (next == GC_DINF && hop + 1 < BFS_CHAIN_HOPS) next = y[k];
+                            else thread_stage(y[k], deg[k], nq, nxt, sg);
+                        }
+                    }
+                    if (next == GC_DINF) break;
+                    x = next;
+                }
+            }
+            stage_flush(nq, nxt, sg);
+        } else if (topdown) {              // one warp per frontier vertex claims unvisited neighbours
             // a large frontier reads a neighbour's distance before trying to
             // claim it (most are taken: a load is cheaper than a failed CAS);
             // a small one, latency-bound, goes straight to the CAS
