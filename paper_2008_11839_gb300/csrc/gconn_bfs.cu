@@ -30,7 +30,7 @@ constexpr uint64_t BEAMER_BETA = 24;    // bottom-up -> top-down when n_f < n / 
 
 struct alignas(128) BfsSlot {    // a line per slot: appends to one do not slow reads of another
     uint32_t qlen;                 // frontier length
-    uint32_t pad;
+    uint32_t heavy;                // a chained level queued a row too long to chain
     unsigned long long degsum;     // arcs out of the frontier
 };
 
@@ -54,6 +54,7 @@ constexpr uint32_t BFS_PROBE_MIN = 16384;   // frontier size from which claims p
 constexpr uint32_t BFS_CHAIN_MAX = 1u << 18;  // frontier size up to which levels chain
 constexpr uint64_t BFS_CHAIN_DEG = 8;         // ... when the frontier's mean degree is at most this
 constexpr uint32_t BFS_CHAIN_HOPS = 16;
+constexpr uint32_t BFS_CHAIN_ARCS = 64;       // a row longer than this is left to a warp-per-vertex level
 struct BfsStage {
     uint32_t cnt;                  // claims staged (may pass BFS_STAGE: the rest went to the queue)
     uint32_t base;                 // the block's reservation on the queue
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(BFS_BLOCK, 8) k_bfs(const OffT* __restrict__ o
     __shared__ BfsStage sg;
     __shared__ uint32_t s_flen;
     __shared__ unsigned long long s_mf;
+    __shared__ uint32_t s_heavy;
     if (threadIdx.x == 0) {
         sg.cnt = 0;
         sg.deg = 0;
@@ -208,10 +210,12 @@ __global__ void __launch_bounds__(BFS_BLOCK, 8) k_bfs(const OffT* __restrict__ o
         if (threadIdx.x == 0) {            // one read of the level's counters per block
             s_flen = __ldcg(&cur->qlen);
             s_mf = __ldcg(&cur->degsum);
+            s_heavy = __ldcg(&cur->heavy);
         }
         __syncthreads();
         const uint32_t flen = s_flen;
         const uint64_t mf = s_mf;
+        const bool heavy = s_heavy != 0;
         if (flen == 0) break;
         if (level > n) {
             if (tid == 0) atomicOr(err, GC_DERR_NONCONV);
@@ -224,8 +228,9 @@ __global__ void __launch_bounds__(BFS_BLOCK, 8) k_bfs(const OffT* __restrict__ o
             BfsSlot* clr = &c->slot[(level + 2) % 3];
             clr->qlen = 0;
             clr->degsum = 0;
+            clr->heavy = 0;
         }
-        if (topdown && flen <= BFS_CHAIN_MAX && mf <= BFS_CHAIN_DEG * (uint64_t)flen) {
+        if (topdown && !heavy && flen <= BFS_CHAIN_MAX && mf <= BFS_CHAIN_DEG * (uint64_t)flen) {
             // a thread per frontier vertex, chained: BFS sampling needs the
             // reached set, not exact levels, so a vertex claimed here may be
             // expanded at once (its neighbours are claimed with the same
@@ -236,6 +241,16 @@ __global__ void __launch_bounds__(BFS_BLOCK, 8) k_bfs(const OffT* __restrict__ o
                 uint32_t x = __ldcg(q + i);
                 for (uint32_t hop = 0; hop < BFS_CHAIN_HOPS; ++hop) {
                     const uint64_t lo = off[x], hi = off[x + 1];
+                    if (hi - lo > BFS_CHAIN_ARCS) {
+                        // no thread scans a long row alone: queue the vertex
+                        // again, marked as a member of the next frontier (a
+                        // bottom-up level looks for exactly that mark), and
+                        // keep the next level warp-per-vertex
+                        dist[x] = level + 1;
+                        thread_stage(x, hi - lo, nq, nxt, sg);
+                        nxt->heavy = 1;
+                        break;
+                    }
                     uint32_t next = GC_DINF;
                     for (uint64_t a0 = lo; a0 < hi; a0 += 4) {
                         // four arcs at a time: their columns, then their

@@ -113,6 +113,39 @@ def test_bfs_staged_claims_overflow(combo):
     assert (host_u32(lab) == ref).all()
 
 
+def _two_hubs():
+    """Hub A with 20,000 leaves, hub B with 10,000, A-B joined, plus a path of
+    300 vertices hanging off one of A's leaves, ids permuted.  Wherever the
+    BFS starts, B enters a frontier together with A's leaves: a level of low
+    mean degree that holds one vertex of degree 10,001."""
+    rng = np.random.default_rng(5)
+    A, B = 0, 1
+    la = np.arange(2, 20002)
+    lb = np.arange(20002, 30002)
+    path = np.arange(30002, 30302)
+    e = np.concatenate([np.stack([np.full(len(la), A), la], 1), np.stack([np.full(len(lb), B), lb], 1),
+                        np.array([[A, B], [la[7], path[0]]]), np.stack([path[:-1], path[1:]], 1)])
+    n = 30302 + 11                              # and eleven isolated vertices
+    perm = rng.permutation(n).astype(np.uint32)
+    e = perm[e].astype(np.uint32)
+    rng.shuffle(e)
+    return n, e
+
+
+@pytest.mark.parametrize("combo", UF_FOREST, ids=combo_id)
+def test_bfs_hub_in_low_degree_frontier(combo):
+    link, f, sp = combo
+    n, e = _two_hubs()
+    ref = oracle.cc_uf(n, e)
+    off, cols = graphgen.csr(n, e)
+    v = g.make_variant(sample="bfs", link=link, find=f, splice=sp)
+    assert (_cc_csr(n, off, cols, v) == ref).all()
+    ids, lab = g.spanning_forest_csr(n, dev(off), dev(cols), v, labels=True)
+    g.gconn_sync()
+    assert oracle.sf_check_arcs(n, off, cols, ids.cpu().numpy().astype(np.uint64), ref) == 0
+    assert (host_u32(lab) == ref).all()
+
+
 def _dense_graph():
     """Two cliques of 1,200 vertices (~1.44 M edges) plus a path, ids permuted:
     without sampling every vertex is active with 1,199 arcs (5 tasks of 256
