@@ -258,3 +258,97 @@ def test_abandoned_union_resumes_from_its_current_pair(splice):
             else:
                 lost |= not same
     assert lost == (splice == "splice")
+
+
+def _chained_bfs(off, cols, s, hops, arcs_cap, bottom_up, rng):
+    """A sequential run of BFS sampling in the chained form (the BFS reading):
+    on a chained level a frontier vertex is expanded and then one of its
+    fresh claims right away, up to `hops` vertices; a row longer than
+    `arcs_cap` is not scanned in a chain but queued again (marked for the next
+    level) and the next level expands whole frontier vertices; levels in
+    `bottom_up` let every unreached vertex look for a neighbour marked with the
+    current level.  Frontier order is shuffled to stand in for concurrency.
+    Returns the level marks and each reached vertex's recorded arc."""
+    n = len(off) - 1
+    inf = -1
+    dist, par = [inf] * n, [None] * n
+    dist[s] = 0
+    frontier, level, heavy = [s], 0, False
+    while frontier:
+        nxt, nheavy = [], False
+        if level in bottom_up:
+            for v in range(n):
+                if dist[v] == inf:
+                    for a in range(off[v], off[v + 1]):
+                        if dist[cols[a]] == level:
+                            dist[v], par[v] = level + 1, a
+                            nxt.append(v)
+                            break
+        else:
+            order = list(frontier)
+            rng.shuffle(order)
+            for x in order:
+                for hop in range(hops if not heavy else 1):
+                    if not heavy and off[x + 1] - off[x] > arcs_cap:
+                        dist[x] = level + 1
+                        nxt.append(x)
+                        nheavy = True
+                        break
+                    nv = None
+                    for a in range(off[x], off[x + 1]):
+                        y = int(cols[a])
+                        if dist[y] == inf:
+                            dist[y], par[y] = level + 1, a
+                            if nv is None and not heavy and hop + 1 < hops:
+                                nv = y
+                            else:
+                                nxt.append(y)
+                    if nv is None:
+                        break
+                    x = nv
+        frontier, heavy, level = nxt, nheavy, level + 1
+    return dist, par
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_chained_bfs_reaches_the_component_with_a_valid_tree(seed):
+    """The BFS reading: chaining, re-queued long rows and bottom-up levels
+    that take any vertex marked in the last level as a parent reach exactly
+    the source's component, and the recorded arcs form a spanning tree of it."""
+    rng = np.random.default_rng(seed)
+    import random
+    prng = random.Random(seed)
+    graphs = GRAPHS[:5] + [(400, graphgen.ba(400, 3, 5 + seed)) if hasattr(graphgen, "ba") else GRAPHS[0]]
+    for n, e in graphs:
+        if n == 0 or len(e) == 0:
+            continue
+        off, cols = graphgen.csr(n, e)
+        s = int(rng.integers(n))
+        hops = int(rng.integers(1, 17))
+        cap = int(rng.integers(1, 9))
+        bottom_up = set(int(x) for x in rng.integers(0, 12, size=int(rng.integers(0, 4))))
+        dist, par = _chained_bfs(off, cols, s, hops, cap, bottom_up, prng)
+        lab = oracle.cc_uf(n, e)
+        reached = {v for v in range(n) if dist[v] != -1}
+        assert reached == {v for v in range(n) if lab[v] == lab[s]}
+        # the recorded arcs: one per reached vertex but the source, each an arc
+        # between two reached vertices, together acyclic
+        owner = np.searchsorted(off, np.arange(len(cols)), side="right") - 1
+        parent = list(range(n))
+
+        def root(x):
+            while parent[x] != x:
+                parent[x] = parent[parent[x]]
+                x = parent[x]
+            return x
+        arcs = [par[v] for v in reached if v != s]
+        assert None not in arcs and len(arcs) == len(reached) - 1
+        for v in reached:
+            if v == s:
+                continue
+            a = par[v]
+            u, w = int(owner[a]), int(cols[a])
+            assert v in (u, w) and u in reached and w in reached
+            ru, rw = root(u), root(w)
+            assert ru != rw
+            parent[ru] = rw
