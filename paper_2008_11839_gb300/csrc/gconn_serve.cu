@@ -562,8 +562,17 @@ extern "C" gconn_status gconn_server_submit(gconn_server* S, uint32_t session, i
     // where the kernels can use the client's buffers in place (device memory,
     // or host memory the device reads directly), a step skips its staging
     auto usable = [](const void* p) -> const void* { return !p ? nullptr : is_device_ptr(p) ? p : host_direct(p); };
+    // the pointer queries answer for the calling thread's current device: ask
+    // as the server's device, then give the caller its device back
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+        cudaGetLastError();
+        prev = -1;
+    }
+    if (prev != S->device) cudaSetDevice(S->device);
     const uint32_t* d_pairs = (const uint32_t*)usable(pairs);
     uint8_t* d_result = op == GCONN_OP_QUERY ? (uint8_t*)usable(result) : nullptr;
+    if (prev >= 0 && prev != S->device) cudaSetDevice(prev);
     std::lock_guard<std::mutex> lk(S->mu);
     auto it = S->sessions.find(session);
     if (it == S->sessions.end() || it->second.closing) return GCONN_E_INVAL;
